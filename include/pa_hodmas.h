@@ -1,0 +1,182 @@
+/*
+ * pa_hodmas.h -- C ABI of the GB300 (sm_103a) higher-order delay-multiply-
+ * and-sum photoacoustic beamformer.
+ *
+ * Method: Mulani, Paul, Singh, "Higher-order correlation based real-time
+ * beamforming in photoacoustic imaging" (arXiv 2203.14906).
+ *   - DAS                         Eq. 1   (Section 2.1)
+ *   - DMAS, real-time O(N) form   Eqs. 2, 3 (Section 2.2)
+ *   - DMAS-k, k = 3, 4, 5         Eqs. 4-6, O(N) forms Eqs. 7-9
+ *                                 (Section 2.3); any k <= 8 by the same
+ *                                 Newton-identity recursion (Section 6 notes
+ *                                 higher orders are possible)
+ *   - band-pass, Hilbert envelope, log compression   (Section 3)
+ *   - delays precomputed into GPU global memory        (Section 5)
+ *
+ * Conventions the paper leaves open (stated once here, used everywhere):
+ *   geometry  element i at x_i = (i - (N-1)/2) * pitch, z = 0; pixel (j, l)
+ *             centre x = x0 + (j + 1/2)(x1 - x0)/nx, z = z0 + (l + 1/2)(z1 - z0)/nz
+ *   delay     one-way time of flight, tau = fs (r / c - t0) samples
+ *   sample    linear interpolation s = r[n] + a (r[n+1] - r[n]), n = floor(tau);
+ *             s = 0 when n < 0 or n + 1 > Ns - 1 (the channel drops out)
+ *   apodise   f_number > 0: element active iff |x_i - x| <= z / (2F),
+ *             weight cos^2(pi (x_i - x) F / z), applied to s before the root
+ *   root      x_i = sgn(s_i) |s_i|^(1/k) (signed even roots as in Eqs. 2, 5;
+ *             real odd roots as in Eqs. 4, 6)
+ *   combine   e_k of the x_i by Newton's identities from power sums, in FP64
+ *   post      per depth column: zero-pad to M = 2^ceil(log2 nz), FFT, multiply
+ *             by a raised-cosine band (f0 +- f0/2 for DAS and odd orders,
+ *             2 f0 +- f0/2 for even orders, roll-off f0/4, clipped at the
+ *             axial Nyquist c / (2 dz)) times the analytic-signal mask,
+ *             inverse FFT, modulus; log = 20 log10(env / image max),
+ *             clipped to [-dyn_range_db, 0].
+ *
+ * Threading: a plan is not thread-safe; use one plan per host thread or
+ * lock around it.  Functions never throw; failures return a status and
+ * pa_last_error() gives a thread-local message.
+ */
+#ifndef PA_HODMAS_H
+#define PA_HODMAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PA_OK = 0,
+  PA_EINVAL = 1,        /* bad argument: sizes, order, null pointer       */
+  PA_ENOMEM = 2,        /* device allocation failed or budget exceeded    */
+  PA_ECUDA = 3,         /* CUDA runtime error (pa_last_error has detail)  */
+  PA_ETIMEOUT = 4,      /* a bounded wait ran out                         */
+  PA_EUNSUPPORTED = 5,  /* valid request outside what this build handles  */
+  PA_EBUSY = 6          /* resource in use (e.g. server queue full)       */
+} pa_status;
+
+typedef enum { PA_RF_F32 = 0, PA_RF_BF16 = 1, PA_RF_F16 = 2 } pa_rf_dtype;
+
+/* Output images (bit mask).  Planes of one frame are ordered DAS, DMAS,
+ * HODMAS, keeping only the requested ones. */
+enum { PA_OUT_DAS = 1u, PA_OUT_DMAS = 2u, PA_OUT_HODMAS = 4u };
+/* Stages written (bit mask), ordered RAW, ENV, LOG. */
+enum { PA_STAGE_RAW = 1u, PA_STAGE_ENV = 2u, PA_STAGE_LOG = 4u };
+
+/* Plan descriptor.  All lengths in metres, times in seconds. */
+typedef struct {
+  int32_t n_elem;        /* N >= 1 array elements                           */
+  double pitch_m;        /* element pitch > 0                               */
+  double c_m_s;          /* speed of sound > 0                              */
+  double fs_hz;          /* RF sample rate > 0                              */
+  double t0_s;           /* time of RF sample 0 after the laser shot        */
+  int32_t n_samples;     /* Ns >= 2 samples per channel                     */
+  int32_t nx, nz;        /* image grid >= 1                                 */
+  double x0_m, x1_m;     /* lateral extent, x1 > x0; (x1-x0)/nx must divide
+                            the pitch: pitch / dx = integer m in 1..32      */
+  double z0_m, z1_m;     /* depth extent, 0 <= z0 < z1                      */
+  int32_t order_k;       /* 1..8; 1 = DAS only, 2 = DMAS                    */
+  uint32_t outputs;      /* PA_OUT_* mask, non-zero                         */
+  pa_rf_dtype rf_dtype;  /* RF storage type; arithmetic is FP32 regardless  */
+  int32_t max_batch;     /* frames per launch; <= 0 means 1                 */
+  double f_number;       /* 0 = full aperture; > 0 dynamic aperture + Hann  */
+  double f0_hz;          /* pulse centre frequency (post-filter band)       */
+  double band_lo_hz;     /* both > 0: explicit band for every output;
+                            otherwise the order-dependent default band      */
+  double band_hi_hz;     /* < 0: band-pass off (analytic mask only)         */
+  double dyn_range_db;   /* log-compression range; <= 0 means 60 dB        */
+  int32_t compensated;   /* 1: Kahan-compensated FP32 power sums            */
+} pa_plan_desc;
+
+typedef struct pa_plan_s* pa_plan_t;
+
+/* Read-only facts about a plan (for tests, benchmarks and admission). */
+typedef struct {
+  int32_t lattice_m;          /* pitch / lateral pixel pitch               */
+  int32_t tile_x, tile_z;     /* pixel tile of one thread block            */
+  int32_t window;             /* RF samples staged per channel per tile    */
+  int32_t n_tiles;            /* tiles per frame                           */
+  int32_t threads;            /* threads per beamforming block             */
+  int32_t blocks_per_sm;      /* resident beamforming blocks per SM        */
+  int32_t fft_size;           /* M                                         */
+  int32_t n_outputs;          /* popcount(outputs)                         */
+  uint32_t warnings;          /* bit k set: output plane k's band lies above
+                                 the axial Nyquist rate (DC removal only)  */
+  int64_t nominal_pairs;      /* nx * nz * N per frame                     */
+  int64_t active_pairs;       /* pairs with non-zero apodisation weight    */
+  int64_t executed_pairs;     /* pairs the kernel evaluates per frame      */
+  size_t device_bytes;        /* device memory owned by the plan now       */
+  uint32_t device_error_flags; /* bounds-check flags raised by device code
+                                  since the plan was built (0 = none; only
+                                  checked builds raise them).  Reading it
+                                  synchronises the device.                 */
+} pa_plan_info;
+
+/*
+ * pa_plan -- validate the descriptor, build the resident delay /
+ * apodisation table on the device (Section 5 computes every pixel/element
+ * delay before the beamforming launch and keeps it in GPU global memory),
+ * the per-tile RF
+ * windows and the post-filter masks.  Work is issued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream) and the call synchronises it
+ * once before returning.  On success *out owns all device memory it
+ * allocated until pa_destroy.
+ * Errors: PA_EINVAL (null pointer, sizes, order outside 1..8, N < k, z0 < 0,
+ * non-integer pitch / dx), PA_EUNSUPPORTED (lattice m > 32, RF window too
+ * large for shared memory), PA_ENOMEM, PA_ECUDA.
+ */
+pa_status pa_plan(const pa_plan_desc* desc, void* cuda_stream, pa_plan_t* out);
+
+/* Bytes of device memory a plan for desc holds, plus the RF and output
+ * buffers of n_frames frames with all stages (for admission control). */
+pa_status pa_plan_footprint(const pa_plan_desc* desc, int32_t n_frames,
+                            size_t* bytes);
+
+pa_status pa_plan_get_info(pa_plan_t plan, pa_plan_info* info);
+
+/*
+ * pa_beamform -- the hot path (Sections 2-3 and 5) on n_frames frames that
+ * are already in device memory.
+ *   rf_dev   [n_frames][N][Ns] RF, contiguous, in desc->rf_dtype; device
+ *            pointer aligned to 16 bytes.  Caller-owned, read only.
+ *   out_dev  [n_frames][n_stages][n_outputs][nx][nz] FP32, z fastest;
+ *            n_stages = popcount(stages), n_outputs = popcount(outputs);
+ *            device pointer aligned to 16 bytes.  Caller-owned.
+ *   stages   PA_STAGE_* mask, non-zero.
+ * Asynchronous on cuda_stream (no host synchronisation); RF and output
+ * buffers must stay valid until the stream reaches this point.  Frames
+ * beyond max_batch are processed in consecutive launches.  n_frames == 0
+ * is a no-op.  Per-pixel channel order is fixed, so a frame's result does
+ * not depend on which other frames share its launch.
+ * Errors: PA_EINVAL (null plan / pointer, n_frames < 0, bad stages),
+ * PA_ECUDA (launch failure; the stream may hold earlier work).
+ */
+pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
+                      float* out_dev, uint32_t stages, void* cuda_stream);
+
+/*
+ * pa_beamform_host -- same computation on HOST buffers (same layouts): the
+ * call copies RF host->device, runs the hot path and copies the output
+ * device->host, then synchronises cuda_stream, so out_host is complete on
+ * return.  Copies overlap with compute across frames.  Pinned (page-locked)
+ * host memory gives the full copy rate.  Device staging buffers are
+ * allocated on first use and owned by the plan.
+ */
+pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
+                           int32_t n_frames, float* out_host, uint32_t stages,
+                           void* cuda_stream);
+
+/* Frees everything the plan owns after synchronising the streams it used.
+ * NULL is accepted (no-op). */
+pa_status pa_destroy(pa_plan_t plan);
+
+const char* pa_status_str(pa_status status);
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* pa_last_error(void);
+/* ABI version (major * 100 + minor). */
+int32_t pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_HODMAS_H */

@@ -1,0 +1,230 @@
+"""ctypes binding of the C ABI declared in ``include/pa_hodmas.h``.
+
+Argument marshalling only: every step of the beamformer runs in the CUDA
+library.  There is no CPU fallback; if the library cannot be built or
+loaded, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_libs: dict = {}
+
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EUNSUPPORTED, PA_EBUSY = range(7)
+PA_RF_F32, PA_RF_BF16, PA_RF_F16 = 0, 1, 2
+PA_OUT_DAS, PA_OUT_DMAS, PA_OUT_HODMAS = 1, 2, 4
+PA_STAGE_RAW, PA_STAGE_ENV, PA_STAGE_LOG = 1, 2, 4
+
+RF_DTYPES = {"f32": PA_RF_F32, "bf16": PA_RF_BF16, "f16": PA_RF_F16}
+
+# Every symbol the header declares (checked by the load test).
+EXPORTS = (
+    "pa_plan",
+    "pa_plan_footprint",
+    "pa_plan_get_info",
+    "pa_beamform",
+    "pa_beamform_host",
+    "pa_destroy",
+    "pa_status_str",
+    "pa_last_error",
+    "pa_version",
+)
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_elem", ctypes.c_int32),
+        ("pitch_m", ctypes.c_double),
+        ("c_m_s", ctypes.c_double),
+        ("fs_hz", ctypes.c_double),
+        ("t0_s", ctypes.c_double),
+        ("n_samples", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("x0_m", ctypes.c_double),
+        ("x1_m", ctypes.c_double),
+        ("z0_m", ctypes.c_double),
+        ("z1_m", ctypes.c_double),
+        ("order_k", ctypes.c_int32),
+        ("outputs", ctypes.c_uint32),
+        ("rf_dtype", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("f_number", ctypes.c_double),
+        ("f0_hz", ctypes.c_double),
+        ("band_lo_hz", ctypes.c_double),
+        ("band_hi_hz", ctypes.c_double),
+        ("dyn_range_db", ctypes.c_double),
+        ("compensated", ctypes.c_int32),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("lattice_m", ctypes.c_int32),
+        ("tile_x", ctypes.c_int32),
+        ("tile_z", ctypes.c_int32),
+        ("window", ctypes.c_int32),
+        ("n_tiles", ctypes.c_int32),
+        ("threads", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
+        ("fft_size", ctypes.c_int32),
+        ("n_outputs", ctypes.c_int32),
+        ("warnings", ctypes.c_uint32),
+        ("nominal_pairs", ctypes.c_int64),
+        ("active_pairs", ctypes.c_int64),
+        ("executed_pairs", ctypes.c_int64),
+        ("device_bytes", ctypes.c_size_t),
+        ("device_error_flags", ctypes.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def load(checked: bool = False, build: bool = True):
+    """Load (building if stale) the CUDA library; raises if unavailable."""
+    key = bool(checked)
+    with _lock:
+        if key in _libs:
+            return _libs[key]
+        path = _build.build(checked=checked) if build else _build.lib_path(checked)
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA beamformer library missing: {path}")
+        L = ctypes.CDLL(path)
+        vp, i32, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+        D = ctypes.POINTER(PlanDesc)
+        L.pa_plan.argtypes = [D, vp, ctypes.POINTER(vp)]
+        L.pa_plan.restype = ctypes.c_int
+        L.pa_plan_footprint.argtypes = [D, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.pa_plan_footprint.restype = ctypes.c_int
+        L.pa_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.pa_plan_get_info.restype = ctypes.c_int
+        L.pa_beamform.argtypes = [vp, vp, i32, vp, u32, vp]
+        L.pa_beamform.restype = ctypes.c_int
+        L.pa_beamform_host.argtypes = [vp, vp, i32, vp, u32, vp]
+        L.pa_beamform_host.restype = ctypes.c_int
+        L.pa_destroy.argtypes = [vp]
+        L.pa_destroy.restype = ctypes.c_int
+        L.pa_status_str.argtypes = [ctypes.c_int]
+        L.pa_status_str.restype = ctypes.c_char_p
+        L.pa_last_error.argtypes = []
+        L.pa_last_error.restype = ctypes.c_char_p
+        L.pa_version.argtypes = []
+        L.pa_version.restype = i32
+        _libs[key] = L
+        return L
+
+
+def check(L, status):
+    if status != PA_OK:
+        raise PAError(status, f"{L.pa_status_str(status).decode()}: {L.pa_last_error().decode()}")
+
+
+def make_desc(wl: dict, order_k=None, outputs=7, rf_dtype=None, max_batch=1,
+              compensated=None) -> PlanDesc:
+    """C descriptor from a workload dictionary (keys as in ``synth.configs``)."""
+    dt = rf_dtype if rf_dtype is not None else wl.get("rf_dtype", "f32")
+    return PlanDesc(
+        n_elem=int(wl["n_elem"]),
+        pitch_m=float(wl["pitch_m"]),
+        c_m_s=float(wl["c_m_s"]),
+        fs_hz=float(wl["fs_hz"]),
+        t0_s=float(wl.get("t0_s", 0.0)),
+        n_samples=int(wl["n_samples"]),
+        nx=int(wl["nx"]),
+        nz=int(wl["nz"]),
+        x0_m=float(wl["x0_m"]),
+        x1_m=float(wl["x1_m"]),
+        z0_m=float(wl["z0_m"]),
+        z1_m=float(wl["z1_m"]),
+        order_k=int(wl["order_k"] if order_k is None else order_k),
+        outputs=int(outputs),
+        rf_dtype=RF_DTYPES[dt] if isinstance(dt, str) else int(dt),
+        max_batch=int(max_batch),
+        f_number=float(wl.get("f_number", 0.0)),
+        f0_hz=float(wl.get("f0_hz", 5e6)),
+        band_lo_hz=float(wl.get("band_lo_hz", 0.0)),
+        band_hi_hz=float(wl.get("band_hi_hz", 0.0)),
+        dyn_range_db=float(wl.get("dyn_range_db", 60.0)),
+        compensated=int(wl.get("compensated", 0) if compensated is None else compensated),
+    )
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Plan:
+    """Resident plan: delay/apodisation table, RF windows, post masks."""
+
+    def __init__(self, desc: PlanDesc, stream=None, checked: bool = False):
+        self._L = load(checked)
+        self.desc = desc
+        h = ctypes.c_void_p()
+        check(self._L, self._L.pa_plan(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        check(self._L, self._L.pa_plan_get_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def out_shape(self, n_frames, stages):
+        n_st = bin(int(stages) & 7).count("1")
+        n_out = bin(int(self.desc.outputs) & 7).count("1")
+        return (n_frames, n_st, n_out, self.desc.nx, self.desc.nz)
+
+    def beamform(self, rf_dev_ptr: int, n_frames: int, out_dev_ptr: int, stages: int, stream=None):
+        """Device-pointer call (pa_beamform); asynchronous on ``stream``."""
+        check(self._L, self._L.pa_beamform(self._h, rf_dev_ptr, int(n_frames), out_dev_ptr,
+                                           int(stages), _stream_handle(stream)))
+
+    def beamform_host(self, rf_host_ptr: int, n_frames: int, out_host_ptr: int, stages: int,
+                      stream=None):
+        """Host-pointer call (pa_beamform_host); returns when output is written."""
+        check(self._L, self._L.pa_beamform_host(self._h, rf_host_ptr, int(n_frames), out_host_ptr,
+                                                int(stages), _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.pa_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def footprint(desc: PlanDesc, n_frames: int, checked: bool = False) -> int:
+    L = load(checked)
+    b = ctypes.c_size_t()
+    check(L, L.pa_plan_footprint(ctypes.byref(desc), int(n_frames), ctypes.byref(b)))
+    return int(b.value)

@@ -1,0 +1,4 @@
+// Order-1 instantiations of the fused beamforming kernel.
+#include "pa_bf_kernel.cuh"
+
+PA_DEFINE_ORDER(1)

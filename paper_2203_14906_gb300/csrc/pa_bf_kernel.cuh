@@ -1,0 +1,421 @@
+// pa_bf_kernel.cuh -- fused delay-gather + interpolation + signed root +
+// power-sum kernel with an FP64 Newton-identity epilogue (Sections 2.1-2.3:
+// Eq. 1 DAS, Eq. 3 real-time DMAS, Eqs. 7-9 O(N) DMAS-k).
+//
+// Work decomposition (one persistent CTA loop over work items):
+//   item   = (pixel tile, residue group, frame), taken from an atomic counter
+//   tile   = tile_x columns x 32 depth rows; lane = depth row
+//   thread = kC pixels of one row at columns jt, jt+m, ..., jt+(kC-1)m, where
+//            m = pitch / dx.  At channel step u, pixel c pairs with channel
+//            i = u + c and all kC pairs share the lattice offset
+//            d = jt - m u, so one delay-table entry (n0, a) serves kC pairs.
+//   chunk  = kNC channel steps; the RF sample window of every channel the
+//            chunk touches is staged in shared memory as overlapping FP32
+//            pairs (r[n], r[n+1]) so one 64-bit LDS fetches both
+//            interpolation taps.  Slots outside [0, Ns-2] hold zeros, which
+//            reproduces the rule "s = 0 when a tap leaves the record".
+// Per pair the arithmetic is FP32: interpolation, apodisation, one MUFU
+// lg2/ex2 (or rsqrt) pair for the roots, power sums; Kahan-compensated
+// sums are folded every kFoldBlocks*kC channels when requested.  The power
+// sums p_1..p_k are turned into e_k by Newton's identities in FP64.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+
+// ---- hardware approximations (PTX instructions, no library code) -------
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Accumulator layout: [0] DAS = sum s, [1] q1 = sum sgn(s)|s|^(1/2),
+// [2] q2 = sum |s|, [3 + (m-1)] p_m = sum x^m for m = 1..k-1.  The last
+// power sum p_k is never accumulated: x^k = s for odd k (p_k = DAS) and
+// x^k = |s| for even k (p_k = q2).
+template <int K>
+struct NAcc {
+  static constexpr int value = (K == 1) ? 1 : (K == 2 ? 3 : K + 2);
+};
+
+template <int K>
+__device__ __forceinline__ void pair_update(float* v, float s) {
+  v[0] += s;
+  if constexpr (K >= 2) {
+    const float as = fabsf(s);
+    v[2] += as;
+    if constexpr (K == 2) {
+      v[1] += copysignf(sqrt_approx(as), s);
+    } else if constexpr (K == 3) {
+      const float y = ex2_approx(lg2_approx(as) * (1.0f / 6.0f));  // |s|^(1/6)
+      const float y2 = y * y;                                      // |s|^(1/3)
+      const float x = copysignf(y2, s);                            // cube root
+      v[1] = fmaf(x, y, v[1]);    // sgn(s)|s|^(1/2)
+      v[3] += x;                  // p1
+      v[4] = fmaf(y2, y2, v[4]);  // p2
+    } else if constexpr (K == 4) {
+      const float y = rsqrt_approx(rsqrt_approx(as));  // |s|^(1/4)
+      const float y2 = y * y;                          // |s|^(1/2)
+      const float x = copysignf(y, s);
+      v[1] = fmaf(x, y, v[1]);    // sgn(s)|s|^(1/2)
+      v[3] += x;                  // p1
+      v[4] += y2;                 // p2
+      v[5] = fmaf(x, y2, v[5]);   // p3
+    } else if constexpr (K == 5) {
+      const float y = ex2_approx(lg2_approx(as) * 0.1f);  // |s|^(1/10)
+      const float y2 = y * y;                             // |s|^(1/5)
+      const float x = copysignf(y2, s);
+      const float x2 = y2 * y2;
+      v[1] = fmaf(x, y2 * y, v[1]);  // x y^3 = sgn(s)|s|^(1/2)
+      v[3] += x;                     // p1
+      v[4] += x2;                    // p2
+      v[5] = fmaf(x, x2, v[5]);      // p3
+      v[6] = fmaf(x2, x2, v[6]);     // p4
+    } else {  // orders 6..8: generic root and powers
+      const float x = copysignf(ex2_approx(lg2_approx(as) * (1.0f / K)), s);
+      v[1] += copysignf(sqrt_approx(as), s);
+      float xp = x;
+      v[3] += x;
+#pragma unroll
+      for (int mm = 2; mm < K; ++mm) {
+        xp *= x;
+        v[2 + mm] += xp;
+      }
+    }
+  }
+}
+
+// Newton's identities in FP64: m e_m = sum_{i=1}^m (-1)^(i-1) e_{m-i} p_i.
+template <int K>
+__device__ __forceinline__ void combine(const double* P, float& das, float& dmas,
+                                        float& ho) {
+  das = (float)P[0];
+  if constexpr (K == 1) {
+    dmas = 0.0f;
+    ho = das;
+  } else {
+    const double dm = 0.5 * fma(P[1], P[1], -P[2]);  // Eq. 3
+    dmas = (float)dm;
+    if constexpr (K == 2) {
+      ho = dmas;
+    } else {
+      double p[K + 1];
+#pragma unroll
+      for (int mm = 1; mm < K; ++mm) p[mm] = P[2 + mm];
+      p[K] = (K & 1) ? P[0] : P[2];
+      double e[K + 1];
+      e[0] = 1.0;
+#pragma unroll
+      for (int mm = 1; mm <= K; ++mm) {
+        double acc = e[mm - 1] * p[1];
+#pragma unroll
+        for (int i = 2; i <= mm; ++i) {
+          const double t = e[mm - i] * p[i];
+          acc = (i & 1) ? acc + t : acc - t;
+        }
+        e[mm] = acc * (1.0 / mm);
+      }
+      ho = (float)e[K];
+    }
+  }
+}
+
+// ---- RF staging ---------------------------------------------------------
+__device__ __forceinline__ float rf_load(const BfParams& p, size_t idx) {
+  if (p.rf_dtype == PA_RF_F32) return __ldg(reinterpret_cast<const float*>(p.rf) + idx);
+  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p.rf) + idx);
+  if (p.rf_dtype == PA_RF_BF16) return __uint_as_float(((unsigned)u) << 16);
+  return __half2float(__ushort_as_half(u));
+}
+
+// Four consecutive samples at row + n (n % 4 == 0, row start aligned).
+__device__ __forceinline__ void rf_load4(const BfParams& p, size_t idx, float* r) {
+  if (p.rf_dtype == PA_RF_F32) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(p.rf) + idx));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  } else {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(p.rf) + idx));
+    const unsigned w[4] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      r[t] = (p.rf_dtype == PA_RF_BF16) ? __uint_as_float(w[t] << 16)
+                                        : __half2float(__ushort_as_half((unsigned short)w[t]));
+    }
+  }
+}
+
+// Stage the sample windows of virtual channels [v0, v0 + kNCS) of one tile.
+// Slot q of staged channel cv holds (r[lo+q], r[lo+q+1]); s_cb[cv] is the
+// shared-memory byte offset of sample 0 of that channel's window, so the
+// pair for sample n0 lives at s_cb[cv] + 8 n0.
+__device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int tile_id,
+                                            int v0, int* s_cb, unsigned char* smem,
+                                            int pairs_off) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int W = p.window, W4 = W >> 2;
+  const int ns = p.n_samples;
+  const int* lo_t = p.lo + (size_t)tile_id * p.nv;
+  for (int cv = warp; cv < kNCS; cv += nwarps) {
+    const int v = v0 + cv;
+    const int i = v + p.u0;
+    const bool in_v = v < p.nv;
+    const int lo = in_v ? __ldg(lo_t + v) : 0;
+    const int slot_off = pairs_off + cv * W * 8;
+    if (lane == 0) s_cb[cv] = slot_off - lo * 8;
+    float4* dst = reinterpret_cast<float4*>(smem + slot_off);
+    const bool real = in_v && i >= 0 && i < p.n_elem;
+    const size_t row = ((size_t)frame * p.n_elem + (real ? i : 0)) * (size_t)ns;
+    for (int q = lane; q < W4; q += 32) {
+      const int n = lo + 4 * q;
+      float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      bool all_valid = false;
+      if (real) {
+        if (p.vec_ok && n >= 0 && n + 4 <= ns - 1) {
+          rf_load4(p, row + n, r);
+          r[4] = rf_load(p, row + n + 4);
+          all_valid = true;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            const int idx = n + t;
+            r[t] = (idx >= 0 && idx < ns) ? rf_load(p, row + idx) : 0.f;
+          }
+        }
+      }
+      float sx[4], sy[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int idx = n + t;
+        const bool ok = all_valid || (idx >= 0 && idx <= ns - 2);
+        sx[t] = ok ? r[t] : 0.f;
+        sy[t] = ok ? r[t + 1] : 0.f;
+      }
+      dst[2 * q] = make_float4(sx[0], sy[0], sx[1], sy[1]);
+      dst[2 * q + 1] = make_float4(sx[2], sy[2], sx[3], sy[3]);
+    }
+  }
+}
+
+template <int NA>
+__device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC][NA],
+                                           float (&cmp)[kC][NA]) {
+#pragma unroll
+  for (int c = 0; c < kC; ++c) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const float y = acc[c][q] - cmp[c][q];
+      const float t = tot[c][q] + y;
+      cmp[c][q] = (t - tot[c][q]) - y;
+      tot[c][q] = t;
+      acc[c][q] = 0.f;
+    }
+  }
+}
+
+template <int K, bool APOD, bool COMP>
+__global__ void __launch_bounds__(256) k_bf_fused(const BfParams p) {
+  constexpr int NA = NAcc<K>::value;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_item = reinterpret_cast<int*>(smem);
+  int* s_cb = reinterpret_cast<int*>(smem + 16);
+  const int pairs_off = 16 + ((kNCS * 4 + 15) & ~15);
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int per_tile = p.ngroups * p.n_frames;
+  const int mstride = p.m * p.table_stride;
+#ifdef PA_CHECK_BOUNDS
+  const int smem_hi = pairs_off + kNCS * p.window * 8 - 8;
+#endif
+
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(p.counter, 1);
+    __syncthreads();
+    const int item = s_item[0];
+    if (item >= p.n_items) break;
+    const int t = item / per_tile;
+    const int rem = item - t * per_tile;
+    const int grp = rem / p.n_frames;
+    const int frame = rem - grp * p.n_frames;
+    const int tz = p.nzt - 1 - t / p.nxt;  // deepest tiles first
+    const int tx = t % p.nxt;
+    const int tile_id = tz * p.nxt + tx;
+    const int sl = grp * nwarps + warp;
+    const int r_m = sl % p.m, g = sl / p.m;
+    const int jt = tx * p.tile_x + g * p.m * kC + r_m;
+    const int z = tz * p.tile_z + lane;
+    const int2 ur = __ldg(p.urange + (size_t)tile_id * p.slots + sl);
+    const int2 vk = __ldg(p.vchunks + (size_t)tile_id * p.ngroups + grp);
+
+    float acc[kC][NA];
+    float tot[COMP ? kC : 1][COMP ? NA : 1];
+    float cmp[COMP ? kC : 1][COMP ? NA : 1];
+#pragma unroll
+    for (int c = 0; c < kC; ++c)
+#pragma unroll
+      for (int q = 0; q < NA; ++q) acc[c][q] = 0.f;
+    if constexpr (COMP) {
+#pragma unroll
+      for (int c = 0; c < kC; ++c)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) tot[c][q] = cmp[c][q] = 0.f;
+    }
+    int fold = 0;
+
+    const int2* tcol = p.table + z;
+    const float* wcol = APOD ? p.wtab + z : nullptr;
+    const int row_u0 = jt - p.dmin;  // table row at channel step u = 0
+
+    for (int k = vk.x; k < vk.y; ++k) {
+      __syncthreads();
+      stage_chunk(p, frame, tile_id, k * kNC, s_cb, smem, pairs_off);
+      __syncthreads();
+      const int cu0 = p.u0 + k * kNC;
+      int u = max(cu0, ur.x);
+      const int u_end = min(cu0 + kNC, ur.y);
+      if (u >= u_end) continue;
+
+      int2 e[kC];
+      float w[kC];
+      {
+        const int r0 = row_u0 - p.m * u;
+#pragma unroll
+        for (int tt = 0; tt < kC; ++tt) {
+#ifdef PA_CHECK_BOUNDS
+          const int rr = r0 - tt * p.m;
+          if (rr < 0 || rr >= p.ndrows) atomicOr(p.err, 1);
+#endif
+          e[tt] = __ldg(tcol + (r0 * p.table_stride - tt * mstride));
+          if constexpr (APOD) w[tt] = __ldg(wcol + (r0 * p.table_stride - tt * mstride));
+        }
+      }
+      for (; u < u_end; u += kC) {
+        int cb[2 * kC - 1];
+        const int cvb = u - cu0;
+#pragma unroll
+        for (int q = 0; q < 2 * kC - 1; ++q) cb[q] = s_cb[cvb + q];
+        int2 en[kC];
+        float wn[kC];
+        const bool more = (u + kC < u_end);
+        if (more) {
+          const int r1 = row_u0 - p.m * (u + kC);
+#pragma unroll
+          for (int tt = 0; tt < kC; ++tt) {
+#ifdef PA_CHECK_BOUNDS
+            const int rr = r1 - tt * p.m;
+            if (rr < 0 || rr >= p.ndrows) atomicOr(p.err, 1);
+#endif
+            en[tt] = __ldg(tcol + (r1 * p.table_stride - tt * mstride));
+            if constexpr (APOD) wn[tt] = __ldg(wcol + (r1 * p.table_stride - tt * mstride));
+          }
+        }
+#pragma unroll
+        for (int tt = 0; tt < kC; ++tt) {
+          const int off = e[tt].x;
+          const float a = __int_as_float(e[tt].y);
+#pragma unroll
+          for (int c = 0; c < kC; ++c) {
+            int addr = cb[tt + c] + off;
+#ifdef PA_CHECK_BOUNDS
+            if (addr < pairs_off || addr > smem_hi) {
+              atomicOr(p.err, 2);
+              addr = pairs_off;
+            }
+#endif
+            const float2 r = *reinterpret_cast<const float2*>(smem + addr);
+            float s = fmaf(a, r.y - r.x, r.x);
+            if constexpr (APOD) s *= w[tt];
+            pair_update<K>(acc[c], s);
+          }
+        }
+        if constexpr (COMP) {
+          if (++fold == kFoldBlocks) {
+            kahan_fold<NA>(acc, tot, cmp);
+            fold = 0;
+          }
+        }
+        if (more) {
+#pragma unroll
+          for (int tt = 0; tt < kC; ++tt) {
+            e[tt] = en[tt];
+            if constexpr (APOD) w[tt] = wn[tt];
+          }
+        }
+      }
+    }
+    if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);
+
+    // ---- FP64 Newton epilogue and store ---------------------------------
+    const size_t plane = (size_t)p.nx * p.nz;
+    const size_t fbase = (size_t)frame * p.planes * plane;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      const int j = jt + p.m * c;
+      if (j < p.nx && z < p.nz) {
+        double P[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          if constexpr (COMP) {
+            P[q] = (double)tot[c][q] - (double)cmp[c][q];
+          } else {
+            P[q] = (double)acc[c][q];
+          }
+        }
+        float das, dmas, ho;
+        combine<K>(P, das, dmas, ho);
+        const size_t px = fbase + (size_t)j * p.nz + z;
+        if (p.plane_das >= 0) p.out[px + (size_t)p.plane_das * plane] = das;
+        if (p.plane_dmas >= 0) p.out[px + (size_t)p.plane_dmas * plane] = dmas;
+        if (p.plane_ho >= 0) p.out[px + (size_t)p.plane_ho * plane] = ho;
+      }
+    }
+  }
+}
+
+}  // namespace pa
+
+// One translation unit per order: launch and occupancy wrappers.
+#define PA_DEFINE_ORDER(K)                                                      \
+  namespace pa {                                                                \
+  static void (*pick_k##K(bool apod, bool comp))(BfParams) {                    \
+    if (apod) return comp ? k_bf_fused<K, true, true> : k_bf_fused<K, true, false>; \
+    return comp ? k_bf_fused<K, false, true> : k_bf_fused<K, false, false>;     \
+  }                                                                             \
+  cudaError_t bf_launch_k##K(bool apod, bool comp, const BfParams& p, int grid, \
+                             int block, size_t smem, cudaStream_t s) {          \
+    void (*f)(BfParams) = pick_k##K(apod, comp);                                \
+    f<<<grid, block, smem, s>>>(p);                                             \
+    return cudaGetLastError();                                                  \
+  }                                                                             \
+  cudaError_t bf_occupancy_k##K(bool apod, bool comp, int block, size_t smem,   \
+                                int* blocks_per_sm) {                           \
+    void (*f)(BfParams) = pick_k##K(apod, comp);                                \
+    cudaError_t e = cudaFuncSetAttribute(                                       \
+        f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);            \
+    if (e != cudaSuccess) return e;                                             \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f,      \
+                                                         block, smem);          \
+  }                                                                             \
+  }

@@ -1,0 +1,109 @@
+// pa_internal.cuh -- types shared by the kernels and the host plan code of
+// the HO-DMAS beamformer (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pa_hodmas.h"
+
+namespace pa {
+
+// Columns handled by one thread.  The thread's pixels sit at columns
+// jt, jt+m, ..., jt+(kC-1)m of one depth row, so at channel step u they all
+// need the delay of the same lattice offset d = jt - m*u (pixel c pairs with
+// channel i = u + c): one table load serves kC pairs.
+constexpr int kC = 4;
+// Channel steps per shared-memory chunk and virtual channels staged per chunk.
+constexpr int kNC = 32;
+constexpr int kNCS = kNC + kC - 1;
+// Channel steps between Kahan folds of the compensated power sums.
+constexpr int kFoldBlocks = 2;  // blocks of kC steps
+constexpr int kMaxOrder = 8;
+constexpr int kMaxThreads = 1024;
+
+// Parameters of the fused gather + interpolate + root + power-sum kernel.
+struct BfParams {
+  const void* rf;         // [frames][N][Ns] in rf_dtype
+  int rf_dtype;           // pa_rf_dtype
+  int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
+  int n_elem, n_samples;
+  long long frame_elems;  // N * Ns
+  const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}
+  const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)
+  int table_stride;       // nz_pad
+  int ndrows;
+  int dmin;               // lattice offset of table row 0
+  int m;                  // pitch / dx
+  int R;                  // column groups per residue in a tile
+  int nxt, nzt;           // tiles along x and z
+  int tile_x, tile_z;
+  int warps;              // warps per block
+  int slots;              // warp slots per tile (m * R)
+  int ngroups;            // residue groups per tile (slots / warps)
+  int nv;                 // virtual channels (zero rows pad both ends)
+  int u0;                 // first channel step (= -(kC-1))
+  int window;             // float2 slots staged per channel (multiple of 4)
+  const int* lo;          // [n_tiles][nv] first staged sample per channel
+  const int2* urange;     // [n_tiles][warps] channel-step range of a warp
+  const int2* vchunks;    // [n_tiles] chunk range of a tile
+  float* out;             // output base
+  int planes;             // planes per frame (n_stages * n_outputs)
+  int plane_das, plane_dmas, plane_ho;  // raw plane of each output or -1
+  int nx, nz;
+  int n_frames;           // frames in this launch
+  int n_items;            // n_tiles * n_frames
+  int* counter;           // work counter (zeroed before launch)
+  int* err;               // bounds-check error word (checked builds)
+};
+
+// Post-filter / envelope parameters (one warp per depth column).
+struct PostParams {
+  float* out;
+  int planes;          // planes per frame
+  int n_out;           // outputs per stage
+  int s_src, s_dst;    // stage index holding raw / receiving the envelope
+  int nx, nz, m, log2m;
+  const float2* tw;    // [m/2] e^{-2 pi i k / m}
+  const float* mask;   // [n_out][m] band-pass x analytic mask
+  int* maxslot;        // [frames][n_out] float bits of the image maximum
+  int n_frames;
+  int warps_per_block;
+};
+
+struct LogParams {
+  float* out;
+  int planes, n_out, s_src, s_dst;
+  long long plane_elems;  // nx * nz
+  const int* maxslot;
+  float dyn_range_db;
+  int n_frames;
+};
+
+// Launchers (one translation unit per order keeps the builds parallel).
+cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p,
+                      int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t bf_occupancy(int order, bool apod, bool comp, int block,
+                         size_t smem, int* blocks_per_sm);
+
+#define PA_DECLARE_ORDER(K)                                                 \
+  cudaError_t bf_launch_k##K(bool apod, bool comp, const BfParams& p,       \
+                             int grid, int block, size_t smem,              \
+                             cudaStream_t s);                               \
+  cudaError_t bf_occupancy_k##K(bool apod, bool comp, int block,            \
+                                size_t smem, int* blocks_per_sm);
+PA_DECLARE_ORDER(1)
+PA_DECLARE_ORDER(2)
+PA_DECLARE_ORDER(3)
+PA_DECLARE_ORDER(4)
+PA_DECLARE_ORDER(5)
+PA_DECLARE_ORDER(6)
+PA_DECLARE_ORDER(7)
+PA_DECLARE_ORDER(8)
+#undef PA_DECLARE_ORDER
+
+cudaError_t post_configure(size_t smem);
+cudaError_t post_launch(const PostParams& p, cudaStream_t s);
+cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s);
+
+}  // namespace pa

@@ -1,0 +1,831 @@
+// pa_plan.cu -- host side of the C ABI: descriptor validation, tile
+// configuration, the plan-time delay / apodisation table kernel (Section 5:
+// delays are computed once and kept resident in device memory), per-tile RF
+// windows, post-filter masks, and the launch sequence of pa_beamform.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pa_internal.cuh"
+
+using namespace pa;
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string g_err;
+
+pa_status fail(pa_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define PA_CUDA(call)                                                         \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return fail(PA_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int popcount3(uint32_t m) { return (int)((m & 1u) + ((m >> 1) & 1u) + ((m >> 2) & 1u)); }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
+// ------------------------------------------------------------------- plan
+struct pa_plan_s {
+  pa_plan_desc d{};
+  int device = 0, num_sms = 0;
+  int K = 1;
+  bool apod = false, comp = false;
+  // tiling
+  int m = 1, R = 1, slots = 1, warps = 1, ngroups = 1, threads = 32;
+  int tile_x = 0, tile_z = 32, nxt = 0, nzt = 0, n_tiles = 0, nx_pad = 0, nz_pad = 0;
+  int u0 = 0, u1 = 0, nv = 0, dmin = 0, ndrows = 0, window = 0;
+  size_t smem = 0;
+  int blocks_per_sm = 0;
+  // post
+  int M = 1, log2M = 0, post_wpb = 1, n_out = 0;
+  int out_id[3] = {-1, -1, -1};  // output slot (0..n_out) of DAS, DMAS, HO
+  uint32_t warnings = 0;
+  float dyn_range = 60.f;
+  // device memory
+  int2* table = nullptr;
+  float* wtab = nullptr;
+  int* lo = nullptr;
+  int2* urange = nullptr;
+  int2* vchunks = nullptr;
+  float2* tw = nullptr;
+  float* mask = nullptr;
+  int* scratch[2] = {nullptr, nullptr};  // [err, counter, maxslots...]
+  size_t scratch_ints = 0;
+  // host-buffer path
+  void* h_rf = nullptr;
+  float* h_out = nullptr;
+  size_t h_rf_bytes = 0, h_out_bytes = 0;
+  cudaStream_t hs[2] = {nullptr, nullptr};
+  cudaEvent_t h_ev = nullptr;
+  // facts
+  int64_t active_pairs = 0, executed_pairs = 0;
+  size_t device_bytes = 0;
+  size_t elt = 4;
+};
+
+namespace {
+
+// ---------------------------------------------------------- plan kernels
+struct TableGeom {
+  int ndrows, nzp, dmin;
+  double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
+  double dx, z0, dz, fs, c, t0, fnum;
+};
+
+// Delay (and apodisation) for every lattice offset d = j - m i and depth row.
+// One-way time of flight in samples, tau = fs (r / c - t0), stored as the
+// integer sample n0 = floor(tau) (pre-scaled by 8, the byte stride of an
+// interpolation pair) and the FP32 fraction a = tau - n0.
+__global__ void k_table(TableGeom g, int2* table, float* wtab) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (z >= g.nzp || row >= g.ndrows) return;
+  const double dxv = g.x_const + ((double)(g.dmin + row) + 0.5) * g.dx;
+  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
+  const double tau = g.fs * (sqrt(dxv * dxv + zp * zp) / g.c - g.t0);
+  double fl = floor(tau);
+  double a = tau - fl;
+  const double lim = 1048576.0;
+  if (fl < -lim) { fl = -lim; a = 0.0; }
+  if (fl > lim) { fl = lim; a = 0.0; }
+  const int n0 = (int)fl;
+  table[(size_t)row * g.nzp + z] = make_int2(n0 * 8, __float_as_int((float)a));
+  if (wtab) {
+    float w = 0.f;
+    const double half = zp / (2.0 * g.fnum);
+    if (half > 0.0 && fabs(dxv) <= half) {
+      const double cw = cos(3.14159265358979323846 * dxv / (2.0 * half));
+      w = (float)(cw * cw);
+    }
+    wtab[(size_t)row * g.nzp + z] = w;
+  }
+}
+
+struct TileGeom {
+  int nxt, nzt, tile_x, tile_z, m, dmin, nzp, nv, u0, ndrows;
+};
+
+// First staged sample (rounded down to a multiple of 4) and window width of
+// every (tile, virtual channel).  The delay grows with depth for z > 0, so the
+// minimum over the tile is on its first row and the maximum on its last.
+__global__ void k_windows(TileGeom g, const int2* table, int* lo, int* wmax, int* err) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (v >= g.nv) return;
+  const int tx = tile % g.nxt, tz = tile / g.nxt;
+  const int i = v + g.u0;
+  const int zf = tz * g.tile_z, zl = zf + g.tile_z - 1;
+  int mn = 0x7fffffff, mx = -0x7fffffff;
+  for (int jj = 0; jj < g.tile_x; ++jj) {
+    const int d = tx * g.tile_x + jj - g.m * i;
+    const int row = d - g.dmin;
+    if (row < 0 || row >= g.ndrows) {
+      atomicOr(err, 4);
+      continue;
+    }
+    mn = min(mn, table[(size_t)row * g.nzp + zf].x >> 3);
+    mx = max(mx, table[(size_t)row * g.nzp + zl].x >> 3);
+  }
+  const int lo_al = mn & ~3;
+  lo[(size_t)tile * g.nv + v] = lo_al;
+  atomicMax(wmax, mx - lo_al + 1);
+}
+
+// Channel-step range of every warp slot.  Without apodisation every step is
+// evaluated; with it, only steps whose lattice offset has a non-zero weight on
+// the warp's deepest row (the widest aperture of its rows).
+__global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wtab,
+                          int2* urange) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (sl >= slots) return;
+  int2 r = make_int2(g.u0, u1);
+  if (wtab) {
+    const int tx = tile % g.nxt, tz = tile / g.nxt;
+    const int r_m = sl % g.m, grp = sl / g.m;
+    const int jt = tx * g.tile_x + grp * g.m * kc + r_m;
+    const int zl = tz * g.tile_z + g.tile_z - 1;
+    int ua = u1, ub = g.u0;
+    for (int u = g.u0; u < u1; ++u) {
+      const int row = jt - g.m * u - g.dmin;
+      if (row < 0 || row >= g.ndrows) continue;
+      if (wtab[(size_t)row * g.nzp + zl] > 0.f) {
+        ua = min(ua, u);
+        ub = max(ub, u + 1);
+      }
+    }
+    if (ua >= ub) {
+      r = make_int2(g.u0, g.u0);
+    } else {
+      ua = g.u0 + ((ua - g.u0) / kc) * kc;
+      ub = g.u0 + ((ub - g.u0 + kc - 1) / kc) * kc;
+      r = make_int2(ua, ub);
+    }
+  }
+  urange[(size_t)tile * slots + sl] = r;
+}
+
+// Pairs with a non-zero apodisation weight (for the active-pair rate).
+__global__ void k_count_active(int nx, int nz, int n, int m, int dmin, int nzp,
+                               const float* wtab, unsigned long long* count) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  unsigned long long c = 0;
+  if (z < nz) {
+    for (int i = 0; i < n; ++i) {
+      const int row = j - m * i - dmin;
+      if (wtab[(size_t)row * nzp + z] > 0.f) ++c;
+    }
+  }
+  for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(0xffffffffu, c, s);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// -------------------------------------------------------- host helpers
+double band_weight(double f, double lo, double hi, double roll) {
+  if (f >= lo && f <= hi) return 1.0;
+  const double u = (f < lo) ? (lo - f) : (f - hi);
+  if (u < roll) return 0.5 * (1.0 + std::cos(M_PI * u / roll));
+  return 0.0;
+}
+
+// Real post-filter mask of one output: raised-cosine band (order-dependent
+// default band, or the descriptor's) times the analytic-signal weights.
+// Returns true when the band lies wholly above the axial Nyquist rate, in
+// which case only DC is removed.
+bool build_mask(const pa_plan_desc& d, bool even_order, int M, float* out) {
+  const double dz = (d.z1_m - d.z0_m) / d.nz;
+  const double f_nyq = d.c_m_s / (2.0 * dz);
+  const double f0 = d.f0_hz;
+  const double roll = 0.25 * f0;
+  const bool off = d.band_hi_hz < 0.0;
+  double lo, hi;
+  if (d.band_lo_hz > 0.0 && d.band_hi_hz > 0.0) {
+    lo = d.band_lo_hz;
+    hi = d.band_hi_hz;
+  } else if (even_order) {
+    lo = 1.5 * f0;
+    hi = 2.5 * f0;
+  } else {
+    lo = 0.5 * f0;
+    hi = 1.5 * f0;
+  }
+  const bool dc_only = !off && lo >= f_nyq;
+  hi = std::min(hi, f_nyq);
+  for (int b = 0; b < M; ++b) {
+    double an = (b == 0 || 2 * b == M) ? 1.0 : (2 * b < M ? 2.0 : 0.0);
+    double bp;
+    if (an == 0.0) bp = 0.0;
+    else if (off) bp = 1.0;
+    else if (dc_only) bp = (b == 0) ? 0.0 : 1.0;
+    else bp = band_weight(d.c_m_s * b / (M * dz), lo, hi, roll);
+    out[b] = (float)(bp * an);
+  }
+  return dc_only;
+}
+
+pa_status validate(const pa_plan_desc* d) {
+  if (!d) return fail(PA_EINVAL, "null descriptor");
+  if (d->n_elem < 1) return fail(PA_EINVAL, "n_elem must be >= 1 (got %d)", d->n_elem);
+  if (d->n_samples < 2) return fail(PA_EINVAL, "n_samples must be >= 2 (got %d)", d->n_samples);
+  if (d->nx < 1 || d->nz < 1) return fail(PA_EINVAL, "empty image grid %dx%d", d->nx, d->nz);
+  if (d->order_k < 1 || d->order_k > kMaxOrder)
+    return fail(PA_EINVAL, "order_k must be in 1..%d (got %d)", kMaxOrder, d->order_k);
+  if (d->n_elem < d->order_k)
+    return fail(PA_EINVAL, "order_k=%d needs at least as many elements (n_elem=%d)", d->order_k,
+                d->n_elem);
+  if (!(d->pitch_m > 0) || !(d->c_m_s > 0) || !(d->fs_hz > 0))
+    return fail(PA_EINVAL, "pitch, c and fs must be positive");
+  if (!(d->x1_m > d->x0_m) || !(d->z1_m > d->z0_m))
+    return fail(PA_EINVAL, "grid extents must be increasing");
+  if (d->z0_m < 0) return fail(PA_EINVAL, "z0 must be >= 0 (pixels in front of the array)");
+  if ((d->outputs & 7u) == 0 || (d->outputs & ~7u))
+    return fail(PA_EINVAL, "outputs mask 0x%x invalid", d->outputs);
+  if (d->rf_dtype != PA_RF_F32 && d->rf_dtype != PA_RF_BF16 && d->rf_dtype != PA_RF_F16)
+    return fail(PA_EINVAL, "rf_dtype %d invalid", (int)d->rf_dtype);
+  if (d->f_number < 0) return fail(PA_EINVAL, "f_number must be >= 0");
+  if (d->f_number > 0 || d->band_hi_hz >= 0) {
+    if (!(d->f0_hz > 0) && !(d->band_lo_hz > 0 && d->band_hi_hz > 0) && d->band_hi_hz >= 0)
+      return fail(PA_EINVAL, "f0_hz must be positive for the default band");
+  }
+  if (d->max_batch > 65535) return fail(PA_EINVAL, "max_batch must be <= 65535");
+  const double dx = (d->x1_m - d->x0_m) / d->nx;
+  const double mr = d->pitch_m / dx;
+  const double mi = std::round(mr);
+  if (mi < 1 || std::fabs(mr - mi) > 1e-6 * mi)
+    return fail(PA_EINVAL,
+                "pitch / lateral pixel pitch = %.9g is not a positive integer; choose x0, x1, "
+                "nx with (x1-x0)/nx = pitch/m",
+                mr);
+  if (mi > 32) return fail(PA_EUNSUPPORTED, "pitch / dx = %d > 32", (int)mi);
+  return PA_OK;
+}
+
+// Tiling from the descriptor alone (no device work).
+void configure(pa_plan_s* P) {
+  const pa_plan_desc& d = P->d;
+  P->K = d.order_k;
+  P->apod = d.f_number > 0;
+  P->comp = d.compensated != 0;
+  const double dx = (d.x1_m - d.x0_m) / d.nx;
+  P->m = (int)std::lround(d.pitch_m / dx);
+  P->R = std::max(1, 4 / P->m);
+  P->slots = P->m * P->R;
+  int B = 1;
+  for (int b = 1; b <= 8; ++b)
+    if (P->slots % b == 0) B = b;
+  P->warps = B;
+  P->ngroups = P->slots / B;
+  P->threads = 32 * B;
+  P->tile_x = P->m * kC * P->R;
+  P->tile_z = 32;
+  P->nxt = (d.nx + P->tile_x - 1) / P->tile_x;
+  P->nzt = (d.nz + P->tile_z - 1) / P->tile_z;
+  P->n_tiles = P->nxt * P->nzt;
+  P->nx_pad = P->nxt * P->tile_x;
+  P->nz_pad = P->nzt * P->tile_z;
+  P->u0 = -(kC - 1);
+  const int steps = ((d.n_elem + kC - 1 + kC - 1) / kC) * kC;  // round N + kC - 1 up
+  P->u1 = P->u0 + steps;
+  const int i_max = P->u1 - 1 + kC - 1;
+  P->nv = i_max - P->u0 + 1;
+  P->dmin = -P->m * i_max;
+  const int dmax = P->nx_pad - 1 + P->m * (kC - 1);
+  P->ndrows = dmax - P->dmin + 1;
+  P->M = 1;
+  P->log2M = 0;
+  while (P->M < d.nz) {
+    P->M <<= 1;
+    ++P->log2M;
+  }
+  P->post_wpb = std::max(1, std::min(8, (int)(65536 / (P->M * (int)sizeof(float2)))));
+  P->n_out = popcount3(d.outputs);
+  int s = 0;
+  for (int o = 0; o < 3; ++o) P->out_id[o] = (d.outputs >> o & 1u) ? s++ : -1;
+  P->dyn_range = d.dyn_range_db > 0 ? (float)d.dyn_range_db : 60.f;
+  P->elt = d.rf_dtype == PA_RF_F32 ? 4 : 2;
+  if (P->d.max_batch <= 0) P->d.max_batch = 1;
+}
+
+size_t table_bytes(const pa_plan_s* P) {
+  size_t b = (size_t)P->ndrows * P->nz_pad * sizeof(int2);
+  if (P->apod) b += (size_t)P->ndrows * P->nz_pad * sizeof(float);
+  b += (size_t)P->n_tiles * P->nv * sizeof(int);
+  b += (size_t)P->n_tiles * P->slots * sizeof(int2);
+  b += (size_t)P->n_tiles * P->ngroups * sizeof(int2);
+  b += (size_t)(P->M / 2 + 1) * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
+  return b;
+}
+
+template <typename T>
+pa_status dalloc(pa_plan_s* P, T** ptr, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA, "cudaMalloc(%zu): %s",
+                n * sizeof(T), cudaGetErrorString(e));
+  }
+  P->device_bytes += n * sizeof(T);
+  return PA_OK;
+}
+
+void free_plan(pa_plan_s* P) {
+  if (!P) return;
+  DeviceGuard g(P->device);
+  for (int s = 0; s < 2; ++s)
+    if (P->hs[s]) cudaStreamSynchronize(P->hs[s]);
+  cudaFree(P->table);
+  cudaFree(P->wtab);
+  cudaFree(P->lo);
+  cudaFree(P->urange);
+  cudaFree(P->vchunks);
+  cudaFree(P->tw);
+  cudaFree(P->mask);
+  cudaFree(P->scratch[0]);
+  cudaFree(P->scratch[1]);
+  cudaFree(P->h_rf);
+  cudaFree(P->h_out);
+  for (int s = 0; s < 2; ++s)
+    if (P->hs[s]) cudaStreamDestroy(P->hs[s]);
+  if (P->h_ev) cudaEventDestroy(P->h_ev);
+  delete P;
+}
+
+pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
+  const pa_plan_desc& d = P->d;
+  PA_CUDA(cudaGetDevice(&P->device));
+  PA_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+
+  pa_status s;
+  if ((s = dalloc(P, &P->table, (size_t)P->ndrows * P->nz_pad)) != PA_OK) return s;
+  if (P->apod && (s = dalloc(P, &P->wtab, (size_t)P->ndrows * P->nz_pad)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->lo, (size_t)P->n_tiles * P->nv)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->urange, (size_t)P->n_tiles * P->slots)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->vchunks, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->tw, (size_t)P->M / 2 + 1)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->mask, (size_t)3 * P->M)) != PA_OK) return s;
+  P->scratch_ints = 2 + (size_t)P->d.max_batch * 3;
+  if ((s = dalloc(P, &P->scratch[0], P->scratch_ints)) != PA_OK) return s;
+  PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
+
+  // delay / apodisation table
+  TableGeom tg;
+  tg.ndrows = P->ndrows;
+  tg.nzp = P->nz_pad;
+  tg.dmin = P->dmin;
+  tg.dx = (d.x1_m - d.x0_m) / d.nx;
+  tg.x_const = d.x0_m + 0.5 * (d.n_elem - 1) * d.pitch_m;
+  tg.z0 = d.z0_m;
+  tg.dz = (d.z1_m - d.z0_m) / d.nz;
+  tg.fs = d.fs_hz;
+  tg.c = d.c_m_s;
+  tg.t0 = d.t0_s;
+  tg.fnum = d.f_number;
+  {
+    dim3 grid((P->nz_pad + 127) / 128, P->ndrows);
+    k_table<<<grid, 128, 0, st>>>(tg, P->table, P->wtab);
+    PA_CUDA(cudaGetLastError());
+  }
+
+  // per-tile windows and warp ranges
+  TileGeom g;
+  g.nxt = P->nxt;
+  g.nzt = P->nzt;
+  g.tile_x = P->tile_x;
+  g.tile_z = P->tile_z;
+  g.m = P->m;
+  g.dmin = P->dmin;
+  g.nzp = P->nz_pad;
+  g.nv = P->nv;
+  g.u0 = P->u0;
+  g.ndrows = P->ndrows;
+  int* wmax = P->scratch[0] + 2;  // borrowed before first use as image maxima
+  {
+    dim3 grid((P->nv + 127) / 128, P->n_tiles);
+    k_windows<<<grid, 128, 0, st>>>(g, P->table, P->lo, wmax, P->scratch[0]);
+    PA_CUDA(cudaGetLastError());
+  }
+  {
+    dim3 grid((P->slots + 31) / 32, P->n_tiles);
+    k_uranges<<<grid, 32, 0, st>>>(g, P->slots, P->u1, kC, P->wtab, P->urange);
+    PA_CUDA(cudaGetLastError());
+  }
+  unsigned long long* cnt = nullptr;
+  if (P->apod) {
+    PA_CUDA(cudaMalloc(&cnt, sizeof(unsigned long long)));
+    PA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    dim3 grid((d.nz + 127) / 128, d.nx);
+    k_count_active<<<grid, 128, 0, st>>>(d.nx, d.nz, d.n_elem, P->m, P->dmin, P->nz_pad,
+                                         P->wtab, cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaFree(cnt);
+      return fail(PA_ECUDA, "k_count_active: %s", cudaGetErrorString(e));
+    }
+  }
+
+  int head[3] = {0, 0, 0};
+  std::vector<int2> ur((size_t)P->n_tiles * P->slots);
+  PA_CUDA(cudaMemcpyAsync(head, P->scratch[0], sizeof head, cudaMemcpyDeviceToHost, st));
+  PA_CUDA(cudaMemcpyAsync(ur.data(), P->urange, ur.size() * sizeof(int2), cudaMemcpyDeviceToHost,
+                          st));
+  unsigned long long active = 0;
+  if (cnt) PA_CUDA(cudaMemcpyAsync(&active, cnt, sizeof active, cudaMemcpyDeviceToHost, st));
+  cudaError_t se = cudaStreamSynchronize(st);
+  if (cnt) cudaFree(cnt);
+  if (se != cudaSuccess) return fail(PA_ECUDA, "plan build: %s", cudaGetErrorString(se));
+  if (head[0] != 0) return fail(PA_ECUDA, "plan build: table row outside range (flag %d)", head[0]);
+  const int width = head[2];
+  P->window = ((std::max(width, 1) + 3) / 4) * 4;
+  PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
+
+  // tile chunk ranges and executed pairs
+  std::vector<int2> vk((size_t)P->n_tiles * P->ngroups);
+  int64_t exec = 0;
+  for (int t = 0; t < P->n_tiles; ++t) {
+    for (int gr = 0; gr < P->ngroups; ++gr) {
+      int ua = P->u1, ub = P->u0;
+      for (int w = 0; w < P->warps; ++w) {
+        const int2 r = ur[(size_t)t * P->slots + gr * P->warps + w];
+        if (r.y > r.x) {
+          ua = std::min(ua, r.x);
+          ub = std::max(ub, r.y);
+          exec += (int64_t)(r.y - r.x) * 32 * kC;
+        }
+      }
+      int2 c = make_int2(0, 0);
+      if (ub > ua) c = make_int2((ua - P->u0) / kNC, (ub - P->u0 + kNC - 1) / kNC);
+      vk[(size_t)t * P->ngroups + gr] = c;
+    }
+  }
+  P->executed_pairs = exec;
+  P->active_pairs = P->apod ? (int64_t)active : (int64_t)d.nx * d.nz * d.n_elem;
+  PA_CUDA(cudaMemcpyAsync(P->vchunks, vk.data(), vk.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                          st));
+
+  // shared memory and occupancy of the fused kernel
+  const size_t pairs_off = 16 + ((kNCS * 4 + 15) & ~15);
+  P->smem = pairs_off + (size_t)kNCS * P->window * sizeof(float2);
+  if (P->smem > 200 * 1024)
+    return fail(PA_EUNSUPPORTED,
+                "RF window of %d samples per channel needs %zu B of shared memory; use a finer "
+                "depth grid",
+                P->window, P->smem);
+  PA_CUDA(bf_occupancy(P->K, P->apod, P->comp, P->threads, P->smem, &P->blocks_per_sm));
+  if (P->blocks_per_sm < 1)
+    return fail(PA_EUNSUPPORTED, "fused kernel does not fit an SM (%d threads, %zu B smem)",
+                P->threads, P->smem);
+
+  // post-filter tables (host FP64 -> FP32)
+  std::vector<float2> tw((size_t)P->M / 2 + 1);
+  for (int k = 0; k <= P->M / 2; ++k) {
+    const double ang = -2.0 * M_PI * (double)k / (double)P->M;
+    tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  std::vector<float> mk((size_t)3 * P->M, 0.f);
+  const bool even_of[3] = {false, true, (P->K % 2) == 0};
+  for (int o = 0; o < 3; ++o) {
+    if (P->out_id[o] < 0) continue;
+    if (build_mask(d, even_of[o], P->M, mk.data() + (size_t)P->out_id[o] * P->M))
+      P->warnings |= 1u << P->out_id[o];
+  }
+  PA_CUDA(cudaMemcpyAsync(P->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+  PA_CUDA(cudaMemcpyAsync(P->mask, mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice,
+                          st));
+  PA_CUDA(post_configure(65536));  // the largest any plan uses (post_wpb * M * 8 <= 64 KiB)
+  PA_CUDA(cudaStreamSynchronize(st));
+  return PA_OK;
+}
+
+int stage_index(uint32_t stages, uint32_t stage) { return popcount3(stages & (stage - 1u)); }
+
+// One launch sequence for nf <= max_batch frames.
+pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                    cudaStream_t st, int* scratch) {
+  const pa_plan_desc& d = P->d;
+  const int n_st = popcount3(stages);
+  const int planes = n_st * P->n_out;
+  const uint32_t raw_stage =
+      (stages & PA_STAGE_RAW) ? PA_STAGE_RAW : ((stages & PA_STAGE_ENV) ? PA_STAGE_ENV : PA_STAGE_LOG);
+  const uint32_t env_stage = (stages & PA_STAGE_ENV) ? PA_STAGE_ENV : PA_STAGE_LOG;
+  const int s_raw = stage_index(stages, raw_stage);
+  const int s_env = stage_index(stages, env_stage);
+
+  PA_CUDA(cudaMemsetAsync(scratch + 1, 0, (1 + (size_t)nf * P->n_out) * sizeof(int), st));
+
+  BfParams b;
+  b.rf = rf;
+  b.rf_dtype = (int)d.rf_dtype;
+  b.vec_ok = (d.n_samples % 4) == 0;
+  b.n_elem = d.n_elem;
+  b.n_samples = d.n_samples;
+  b.frame_elems = (long long)d.n_elem * d.n_samples;
+  b.table = P->table;
+  b.wtab = P->wtab;
+  b.table_stride = P->nz_pad;
+  b.ndrows = P->ndrows;
+  b.dmin = P->dmin;
+  b.m = P->m;
+  b.R = P->R;
+  b.nxt = P->nxt;
+  b.nzt = P->nzt;
+  b.tile_x = P->tile_x;
+  b.tile_z = P->tile_z;
+  b.warps = P->warps;
+  b.slots = P->slots;
+  b.ngroups = P->ngroups;
+  b.nv = P->nv;
+  b.u0 = P->u0;
+  b.window = P->window;
+  b.lo = P->lo;
+  b.urange = P->urange;
+  b.vchunks = P->vchunks;
+  b.out = out;
+  b.planes = planes;
+  b.plane_das = P->out_id[0] >= 0 ? s_raw * P->n_out + P->out_id[0] : -1;
+  b.plane_dmas = P->out_id[1] >= 0 ? s_raw * P->n_out + P->out_id[1] : -1;
+  b.plane_ho = P->out_id[2] >= 0 ? s_raw * P->n_out + P->out_id[2] : -1;
+  b.nx = d.nx;
+  b.nz = d.nz;
+  b.n_frames = nf;
+  b.n_items = P->n_tiles * P->ngroups * nf;
+  b.counter = scratch + 1;
+  b.err = scratch;
+  const int grid = std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms));
+  PA_CUDA(bf_launch(P->K, P->apod, P->comp, b, grid, P->threads, P->smem, st));
+
+  if (stages & (PA_STAGE_ENV | PA_STAGE_LOG)) {
+    PostParams q;
+    q.out = out;
+    q.planes = planes;
+    q.n_out = P->n_out;
+    q.s_src = s_raw;
+    q.s_dst = s_env;
+    q.nx = d.nx;
+    q.nz = d.nz;
+    q.m = P->M;
+    q.log2m = P->log2M;
+    q.tw = P->tw;
+    q.mask = P->mask;
+    q.maxslot = scratch + 2;
+    q.n_frames = nf;
+    q.warps_per_block = P->post_wpb;
+    PA_CUDA(post_launch(q, st));
+  }
+  if (stages & PA_STAGE_LOG) {
+    LogParams l;
+    l.out = out;
+    l.planes = planes;
+    l.n_out = P->n_out;
+    l.s_src = s_env;
+    l.s_dst = stage_index(stages, PA_STAGE_LOG);
+    l.plane_elems = (long long)d.nx * d.nz;
+    l.maxslot = scratch + 2;
+    l.dyn_range_db = P->dyn_range;
+    l.n_frames = nf;
+    PA_CUDA(log_launch(l, P->num_sms, st));
+  }
+  return PA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ dispatchers
+namespace pa {
+cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p, int grid, int block,
+                      size_t smem, cudaStream_t s) {
+  switch (order) {
+    case 1: return bf_launch_k1(apod, comp, p, grid, block, smem, s);
+    case 2: return bf_launch_k2(apod, comp, p, grid, block, smem, s);
+    case 3: return bf_launch_k3(apod, comp, p, grid, block, smem, s);
+    case 4: return bf_launch_k4(apod, comp, p, grid, block, smem, s);
+    case 5: return bf_launch_k5(apod, comp, p, grid, block, smem, s);
+    case 6: return bf_launch_k6(apod, comp, p, grid, block, smem, s);
+    case 7: return bf_launch_k7(apod, comp, p, grid, block, smem, s);
+    case 8: return bf_launch_k8(apod, comp, p, grid, block, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t bf_occupancy(int order, bool apod, bool comp, int block, size_t smem, int* n) {
+  switch (order) {
+    case 1: return bf_occupancy_k1(apod, comp, block, smem, n);
+    case 2: return bf_occupancy_k2(apod, comp, block, smem, n);
+    case 3: return bf_occupancy_k3(apod, comp, block, smem, n);
+    case 4: return bf_occupancy_k4(apod, comp, block, smem, n);
+    case 5: return bf_occupancy_k5(apod, comp, block, smem, n);
+    case 6: return bf_occupancy_k6(apod, comp, block, smem, n);
+    case 7: return bf_occupancy_k7(apod, comp, block, smem, n);
+    case 8: return bf_occupancy_k8(apod, comp, block, smem, n);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace pa
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+pa_status pa_plan(const pa_plan_desc* desc, void* cuda_stream, pa_plan_t* out) {
+  if (!out) return fail(PA_EINVAL, "null output handle");
+  *out = nullptr;
+  pa_status s = validate(desc);
+  if (s != PA_OK) return s;
+  pa_plan_s* P = new (std::nothrow) pa_plan_s();
+  if (!P) return fail(PA_ENOMEM, "host allocation failed");
+  P->d = *desc;
+  configure(P);
+  s = build_plan(P, (cudaStream_t)cuda_stream);
+  if (s != PA_OK) {
+    const std::string keep = g_err;
+    free_plan(P);
+    g_err = keep;
+    return s;
+  }
+  *out = P;
+  return PA_OK;
+}
+
+pa_status pa_plan_footprint(const pa_plan_desc* desc, int32_t n_frames, size_t* bytes) {
+  if (!bytes) return fail(PA_EINVAL, "null bytes pointer");
+  pa_status s = validate(desc);
+  if (s != PA_OK) return s;
+  if (n_frames < 0) return fail(PA_EINVAL, "n_frames < 0");
+  pa_plan_s P;
+  P.d = *desc;
+  configure(&P);
+  size_t b = table_bytes(&P);
+  b += (2 + (size_t)P.d.max_batch * 3) * sizeof(int);
+  const size_t elt = desc->rf_dtype == PA_RF_F32 ? 4 : 2;
+  b += (size_t)n_frames * desc->n_elem * desc->n_samples * elt;
+  b += (size_t)n_frames * 3 * P.n_out * desc->nx * desc->nz * sizeof(float);
+  *bytes = b;
+  return PA_OK;
+}
+
+pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
+  if (!P || !info) return fail(PA_EINVAL, "null argument");
+  info->lattice_m = P->m;
+  info->tile_x = P->tile_x;
+  info->tile_z = P->tile_z;
+  info->window = P->window;
+  info->n_tiles = P->n_tiles;
+  info->threads = P->threads;
+  info->blocks_per_sm = P->blocks_per_sm;
+  info->fft_size = P->M;
+  info->n_outputs = P->n_out;
+  info->warnings = P->warnings;
+  info->nominal_pairs = (int64_t)P->d.nx * P->d.nz * P->d.n_elem;
+  info->active_pairs = P->active_pairs;
+  info->executed_pairs = P->executed_pairs;
+  info->device_bytes = P->device_bytes;
+  info->device_error_flags = 0;
+  {
+    DeviceGuard g(P->device);
+    for (int b = 0; b < 2; ++b) {
+      if (!P->scratch[b]) continue;
+      int flag = 0;
+      PA_CUDA(cudaDeviceSynchronize());
+      PA_CUDA(cudaMemcpy(&flag, P->scratch[b], sizeof flag, cudaMemcpyDeviceToHost));
+      info->device_error_flags |= (uint32_t)flag;
+    }
+  }
+  return PA_OK;
+}
+
+pa_status pa_beamform(pa_plan_t P, const void* rf_dev, int32_t n_frames, float* out_dev,
+                      uint32_t stages, void* cuda_stream) {
+  if (!P) return fail(PA_EINVAL, "null plan");
+  if (n_frames < 0) return fail(PA_EINVAL, "n_frames < 0");
+  if ((stages & 7u) == 0 || (stages & ~7u)) return fail(PA_EINVAL, "stages mask 0x%x invalid", stages);
+  if (n_frames == 0) return PA_OK;
+  if (!rf_dev || !out_dev) return fail(PA_EINVAL, "null buffer");
+  if (((uintptr_t)rf_dev & 15) || ((uintptr_t)out_dev & 15))
+    return fail(PA_EINVAL, "buffers must be 16-byte aligned");
+  DeviceGuard g(P->device);
+  const pa_plan_desc& d = P->d;
+  const size_t rf_frame = (size_t)d.n_elem * d.n_samples * P->elt;
+  const size_t out_frame = (size_t)popcount3(stages) * P->n_out * d.nx * d.nz;
+  for (int f0 = 0; f0 < n_frames; f0 += d.max_batch) {
+    const int nf = std::min(d.max_batch, n_frames - f0);
+    pa_status s = run_chunk(P, (const char*)rf_dev + (size_t)f0 * rf_frame, nf,
+                            out_dev + (size_t)f0 * out_frame, stages, (cudaStream_t)cuda_stream,
+                            P->scratch[0]);
+    if (s != PA_OK) return s;
+  }
+  return PA_OK;
+}
+
+pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, float* out_host,
+                           uint32_t stages, void* cuda_stream) {
+  if (!P) return fail(PA_EINVAL, "null plan");
+  if (n_frames < 0) return fail(PA_EINVAL, "n_frames < 0");
+  if ((stages & 7u) == 0 || (stages & ~7u)) return fail(PA_EINVAL, "stages mask 0x%x invalid", stages);
+  if (n_frames == 0) return PA_OK;
+  if (!rf_host || !out_host) return fail(PA_EINVAL, "null buffer");
+  DeviceGuard g(P->device);
+  const pa_plan_desc& d = P->d;
+  cudaStream_t user = (cudaStream_t)cuda_stream;
+  // chunks small enough that two of them pipeline copy and compute
+  int chunk = std::min(d.max_batch, std::max(1, (n_frames + 3) / 4));
+  const size_t rf_frame = (size_t)d.n_elem * d.n_samples * P->elt;
+  const size_t out_frame = (size_t)popcount3(stages) * P->n_out * d.nx * d.nz;
+  const size_t need_rf = 2 * (size_t)chunk * rf_frame;
+  const size_t need_out = 2 * (size_t)chunk * out_frame * sizeof(float);
+  if (need_rf > P->h_rf_bytes) {
+    cudaFree(P->h_rf);
+    P->device_bytes -= P->h_rf_bytes;
+    P->h_rf_bytes = 0;
+    PA_CUDA(cudaMalloc(&P->h_rf, need_rf));
+    P->h_rf_bytes = need_rf;
+    P->device_bytes += need_rf;
+  }
+  if (need_out > P->h_out_bytes) {
+    cudaFree(P->h_out);
+    P->device_bytes -= P->h_out_bytes;
+    P->h_out_bytes = 0;
+    PA_CUDA(cudaMalloc(&P->h_out, need_out));
+    P->h_out_bytes = need_out;
+    P->device_bytes += need_out;
+  }
+  if (!P->hs[0]) {
+    PA_CUDA(cudaStreamCreateWithFlags(&P->hs[0], cudaStreamNonBlocking));
+    PA_CUDA(cudaStreamCreateWithFlags(&P->hs[1], cudaStreamNonBlocking));
+    PA_CUDA(cudaEventCreateWithFlags(&P->h_ev, cudaEventDisableTiming));
+  }
+  if (!P->scratch[1]) {
+    pa_status s = dalloc(P, &P->scratch[1], P->scratch_ints);
+    if (s != PA_OK) return s;
+    PA_CUDA(cudaMemset(P->scratch[1], 0, P->scratch_ints * sizeof(int)));
+  }
+  // the internal streams start after work already queued on the caller's stream
+  PA_CUDA(cudaEventRecord(P->h_ev, user));
+  PA_CUDA(cudaStreamWaitEvent(P->hs[0], P->h_ev, 0));
+  PA_CUDA(cudaStreamWaitEvent(P->hs[1], P->h_ev, 0));
+  int c = 0;
+  for (int f0 = 0; f0 < n_frames; f0 += chunk, ++c) {
+    const int nf = std::min(chunk, n_frames - f0);
+    const int b = c & 1;
+    cudaStream_t st = P->hs[b];
+    char* rf_d = (char*)P->h_rf + (size_t)b * chunk * rf_frame;
+    float* out_d = P->h_out + (size_t)b * chunk * out_frame;
+    PA_CUDA(cudaMemcpyAsync(rf_d, (const char*)rf_host + (size_t)f0 * rf_frame, nf * rf_frame,
+                            cudaMemcpyHostToDevice, st));
+    pa_status s = run_chunk(P, rf_d, nf, out_d, stages, st, P->scratch[b]);
+    if (s != PA_OK) return s;
+    PA_CUDA(cudaMemcpyAsync(out_host + (size_t)f0 * out_frame, out_d,
+                            nf * out_frame * sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  PA_CUDA(cudaStreamSynchronize(P->hs[0]));
+  PA_CUDA(cudaStreamSynchronize(P->hs[1]));
+  return PA_OK;
+}
+
+pa_status pa_destroy(pa_plan_t P) {
+  free_plan(P);
+  return PA_OK;
+}
+
+const char* pa_status_str(pa_status s) {
+  switch (s) {
+    case PA_OK: return "ok";
+    case PA_EINVAL: return "invalid argument";
+    case PA_ENOMEM: return "out of device memory";
+    case PA_ECUDA: return "CUDA error";
+    case PA_ETIMEOUT: return "timed out";
+    case PA_EUNSUPPORTED: return "unsupported";
+    case PA_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* pa_last_error(void) { return g_err.c_str(); }
+
+int32_t pa_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+"""Host-side checks of the C ABI that need no GPU.
+
+* The library builds for sm_103a, loads, and exports every function that
+  ``include/*.h`` declares.
+* Descriptor validation rejects bad requests before any device call.
+* The oracle and the CUDA library share no code (no cross includes).
+"""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import synth
+from paper_2203_14906_gb300 import _build, _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(pa_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_function():
+    L = _native.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, f"missing exports: {missing}"
+    assert set(_native.EXPORTS) <= declared
+
+
+def test_version_and_status_strings():
+    L = _native.load()
+    assert L.pa_version() >= 100
+    assert L.pa_status_str(0) == b"ok"
+    assert L.pa_status_str(1) == b"invalid argument"
+
+
+def _status(desc, n_frames=1):
+    L = _native.load()
+    b = ctypes.c_size_t()
+    return L.pa_plan_footprint(ctypes.byref(desc), n_frames, ctypes.byref(b)), b.value
+
+
+def test_validation_rejects_bad_descriptors():
+    wl = synth.workload("cfg1")
+    ok, nbytes = _status(_native.make_desc(wl))
+    assert ok == _native.PA_OK and nbytes > 0
+    bad = [
+        dict(order_k=0),
+        dict(order_k=9),
+        dict(n_elem=2, order_k=3),  # N < k
+        dict(nx=0),
+        dict(nz=0),
+        dict(n_samples=1),
+        dict(z0_m=-1e-3),
+        dict(x1_m=-9.6e-3),  # empty lateral extent
+        dict(nx=100),  # pitch / dx not an integer
+    ]
+    for over in bad:
+        w = dict(wl)
+        w.update(over)
+        if "n_elem" in over:
+            w["x0_m"], w["x1_m"] = -over["n_elem"] * 1.5e-4, over["n_elem"] * 1.5e-4
+            w["nx"] = over["n_elem"] * 2
+        st, _ = _status(_native.make_desc(w, order_k=w["order_k"]))
+        assert st == _native.PA_EINVAL, (over, st)
+    d = _native.make_desc(wl)
+    d.outputs = 0
+    assert _status(d)[0] == _native.PA_EINVAL
+    d = _native.make_desc(wl)
+    d.rf_dtype = 7
+    assert _status(d)[0] == _native.PA_EINVAL
+    # pitch/dx = 64 exceeds the supported lattice
+    w = dict(wl, nx=64 * 64)
+    assert _status(_native.make_desc(w))[0] == _native.PA_EUNSUPPORTED
+
+
+def test_plan_validation_happens_before_device_work():
+    L = _native.load()
+    h = ctypes.c_void_p()
+    d = _native.make_desc(synth.workload("cfg1"), order_k=0)
+    assert L.pa_plan(ctypes.byref(d), None, ctypes.byref(h)) == _native.PA_EINVAL
+    assert b"order_k" in L.pa_last_error()
+    assert L.pa_destroy(None) == _native.PA_OK
+
+
+def test_footprint_grows_with_frames():
+    wl = synth.workload("cfg2")
+    d = _native.make_desc(wl)
+    a = _native.footprint(d, 1)
+    b = _native.footprint(d, 8)
+    assert b > a
+    per = (b - a) / 7
+    want = 128 * 2048 * 4 + 3 * 3 * 512 * 512 * 4
+    assert abs(per - want) < 1e-6 * want + 1
+
+
+def test_oracle_and_cuda_sources_share_nothing():
+    cu = glob.glob(os.path.join(ROOT, "paper_2203_14906_gb300", "csrc", "*"))
+    for f in cu:
+        txt = open(f).read()
+        assert "pa_oracle" not in txt and "oracle/" not in txt, f
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*.[ch]")):
+        txt = open(f).read()
+        assert "pa_hodmas" not in txt and "pa_internal" not in txt, f
+    pkg = glob.glob(os.path.join(ROOT, "paper_2203_14906_gb300", "*.py"))
+    for f in pkg:
+        txt = open(f).read()
+        assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_build_is_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+    assert os.path.exists(_build.build())

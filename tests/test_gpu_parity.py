@@ -1,0 +1,177 @@
+"""GPU (CUDA, sm_103a) vs FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP32 path 1e-4 of the image peak (RAW and ENV), 0.05 dB after
+log compression on pixels within 6 dB of the peak; reduced-precision path
+5e-3 of the peak against the oracle on the unquantised RF.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import assert_parity, compare, oracle_frames, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL_LP = 5e-3
+
+
+def _frames(wl, seeds):
+    return np.stack([synth.make_frame(wl, s) for s in seeds])
+
+
+def test_cfg1_all_seeds_batched_k3():
+    """cfg1 (64 el, 1024 samples, 128x128): five seeded frames in one launch."""
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, wl["seeds"])
+    out, info, deq = run_gpu(wl, rf, 3)
+    assert info["device_error_flags"] == 0
+    res = compare(out, oracle_frames(wl, deq, 3))
+    assert_parity(res, TOL32, what="cfg1 k=3")
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 6, 7, 8])
+def test_cfg1_every_order(k):
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, [1])
+    out, _, deq = run_gpu(wl, rf, k)
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"cfg1 k={k}")
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_cfg2_full_size(k):
+    """cfg2 at full size: 128 el x 2048 samples, 512x512, orders 2..5."""
+    wl = synth.workload("cfg2")
+    rf = _frames(wl, wl["seeds"])
+    out, _, deq = run_gpu(wl, rf, k)
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"cfg2 k={k}")
+
+
+def test_ragged_grid_odd_aperture_unaligned_samples():
+    """Grid not a multiple of the tile, odd N, Ns % 4 != 0 (scalar staging),
+    lattice m = 2, several tiles and ragged tails in both directions."""
+    wl = synth.workload("cfg1", n_elem=37, n_samples=1001, nx=74, nz=77, z1_m=18e-3)
+    wl["x0_m"], wl["x1_m"] = -37 * 0.15e-3, 37 * 0.15e-3
+    rf = _frames(wl, [7, 8])
+    for k in (3, 4):
+        out, info, deq = run_gpu(wl, rf, k, max_batch=1)
+        assert info["lattice_m"] == 2
+        assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"ragged k={k}")
+
+
+def test_pixels_beyond_the_record_and_t0():
+    """Short records (many delays fall off the end) and t0 > 0 (negative
+    delays near the array): those channels must drop out exactly."""
+    wl = synth.workload("cfg1", n_samples=300, t0_s=2.0e-6, nz=96)
+    rf = _frames(wl, [3])
+    out, _, deq = run_gpu(wl, rf, 3)
+    assert_parity(compare(out, oracle_frames(wl, deq, 3)), TOL32, what="invalid delays")
+
+
+@pytest.mark.parametrize("m", [1, 4, 8, 16])
+def test_lattice_factors(m):
+    """Pitch / lateral pixel pitch = m (serving mixes use 1..16)."""
+    n = 32
+    wl = synth.workload("cfg1", n_elem=n, nx=n * m, nz=64, z1_m=12e-3)
+    wl["x0_m"], wl["x1_m"] = -n * 0.15e-3, n * 0.15e-3
+    rf = _frames(wl, [5])
+    out, info, deq = run_gpu(wl, rf, 3)
+    assert info["lattice_m"] == m
+    assert_parity(compare(out, oracle_frames(wl, deq, 3)), TOL32, what=f"m={m}")
+
+
+def test_apodised_cfg5_frames_bf16():
+    """cfg5 geometry (1024x1024, 128 el, F# 1.5 Hann, k=4), BF16 RF with
+    compensated sums: two frames."""
+    wl = synth.workload("cfg5")
+    rf = np.stack([synth.make_frame(wl, 41, f) for f in range(2)])
+    out, info, deq = run_gpu(wl, rf, 4, rf_dtype="bf16", compensated=1)
+    assert info["active_pairs"] < info["nominal_pairs"]
+    assert info["executed_pairs"] < info["nominal_pairs"]
+    ref_deq = oracle_frames(wl, deq, 4)
+    assert_parity(compare(out, ref_deq), TOL32, what="cfg5 vs dequantised")
+    ref = oracle_frames(wl, rf, 4)
+    assert_parity(compare(out, ref), TOL_LP, what="cfg5 vs unquantised")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("k", [3, 5])
+def test_cfg3_precision(dtype, k):
+    """cfg3 (256 el, 4096 samples at 50 MHz, 1024x1024): 16-bit RF, Kahan
+    power sums, FP64 combine; error against the oracle on the unquantised
+    RF (end to end) and on the dequantised RF (compute only)."""
+    wl = synth.workload("cfg3")
+    rf = _frames(wl, wl["seeds"])
+    out, _, deq = run_gpu(wl, rf, k, rf_dtype=dtype, compensated=1)
+    assert_parity(compare(out, oracle_frames(wl, rf, k)), TOL_LP, what=f"cfg3 {dtype} e2e")
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"cfg3 {dtype} compute")
+
+
+def test_all_zero_frame_and_empty_call():
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+
+    wl = synth.workload("cfg1", nx=64, nz=64)
+    out, _, _ = run_gpu(wl, np.zeros((1, 64, 1024)), 3)
+    assert np.all(out[0, :2] == 0.0)
+    assert np.all(out[0, 2] == -60.0)
+    with pa.Plan(pa.make_desc(wl)) as plan:
+        rf = torch.zeros((0, 64, 1024), device="cuda")
+        o = pa.beamform(plan, rf, 7)
+        assert o.shape[0] == 0
+
+
+def test_minimum_aperture_n_equals_k():
+    wl = synth.workload("cfg1", n_elem=5, nx=10, nz=40, z1_m=10e-3)
+    wl["x0_m"], wl["x1_m"] = -5 * 0.15e-3, 5 * 0.15e-3
+    rf = _frames(wl, [2])
+    out, _, deq = run_gpu(wl, rf, 5)
+    assert_parity(compare(out, oracle_frames(wl, deq, 5)), TOL32, what="N=k")
+
+
+def test_stage_and_output_subsets_match_full():
+    """Any subset of stages/outputs gives the same planes as the full call."""
+    wl = synth.workload("cfg1", nx=64, nz=96, z1_m=15e-3)
+    rf = _frames(wl, [4])
+    full, _, _ = run_gpu(wl, rf, 3)
+    for outputs, stages in ((4, 4), (1, 2), (6, 5), (2, 1)):
+        sub, _, _ = run_gpu(wl, rf, 3, outputs=outputs, stages=stages)
+        s_idx = [i for i, b in enumerate((1, 2, 4)) if stages & b]
+        o_idx = [i for i, b in enumerate((1, 2, 4)) if outputs & b]
+        want = full[:, s_idx][:, :, o_idx]
+        assert np.array_equal(sub, want), (outputs, stages)
+
+
+def test_frame_result_independent_of_batch():
+    """A frame alone and inside a batch gives bitwise identical images."""
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, [1, 2, 3])
+    batch, _, _ = run_gpu(wl, rf, 4)
+    for f in range(3):
+        alone, _, _ = run_gpu(wl, rf[f:f + 1], 4)
+        assert np.array_equal(alone[0], batch[f])
+    split, _, _ = run_gpu(wl, rf, 4, max_batch=2)
+    assert np.array_equal(split, batch)
+
+
+def test_host_buffer_path_matches_device_path():
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, [1, 2, 3, 4, 5])
+    dev, _, _ = run_gpu(wl, rf, 3)
+    host, _, _ = run_gpu(wl, rf, 3, host=True, max_batch=2)
+    assert np.array_equal(dev, host)
+
+
+def test_checked_build_raises_no_bounds_flags():
+    """Bounds-checked build of the same kernels over the edge-case geometries."""
+    cases = [
+        (synth.workload("cfg1"), 3, "f32", 0),
+        (synth.workload("cfg1", n_samples=300, t0_s=2e-6, nz=96), 5, "f32", 0),
+        (synth.workload("cfg5", nx=256, nz=256), 4, "bf16", 1),
+    ]
+    for wl, k, dt, comp in cases:
+        rf = synth.make_frame(wl, 1)[None]
+        _, info, _ = run_gpu(wl, rf, k, rf_dtype=dt, compensated=comp, checked=True)
+        assert info["device_error_flags"] == 0, (wl["name"], k)
