@@ -1,0 +1,456 @@
+"""Throughput benchmark of the HO-DMAS hot path (one JSON line on rank 0).
+
+Default workload (cfg2 geometry): 128-element linear array, 0.3 mm pitch,
+2048 samples at 40 MHz, 512 x 512 grid over 38.4 x 40 mm; DAS, DMAS and
+DMAS-3 (k = 3) in the same pass, then band-pass + Hilbert envelope + log
+compression; FP32 RF.  A step beamforms ``--frames`` seeded synthetic frames
+(each rank its own frames) into their displayed log images.
+
+Metric: Gpixel.ch/s = nx * nz * N * frames / time.  ``value`` is device
+time (CUDA events around each step on the launching stream, inputs resident
+in HBM, L2 flushed by a 256 MiB write between steps, outside the events).
+``e2e`` is the same metric through ``pa_beamform_host`` (pinned host RF in,
+log images out, copies inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HO-DMAS k=3 Gpixel·ch/s vs plain FP32 form; serving p50/p99 frame latency ms"
+UNIT = "Gpixel·ch/s"
+CSRC = os.path.join(ROOT, "paper_2203_14906_gb300", "csrc")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=32)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip precision form and cpu baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload():
+    import synth
+
+    return synth.workload("cfg2")
+
+
+def config_dict(args, wl, extra=None):
+    d = {
+        "workload": (
+            f"cfg2 geometry: {wl['n_elem']} el x {wl['n_samples']} samples @ {wl['fs_hz']/1e6:g} MHz, "
+            f"{wl['nx']}x{wl['nz']} grid; DAS+DMAS+DMAS-{args.order} in one pass; band-pass, "
+            "Hilbert envelope, log; FP32 RF"
+        ),
+        "frames_per_step": args.frames,
+        "order_k": args.order,
+        "n_elem": wl["n_elem"],
+        "n_samples": wl["n_samples"],
+        "grid": [wl["nx"], wl["nz"]],
+        "stages": "log (raw and envelope computed in place)",
+        "l2": "flushed between steps by a 256 MiB write (outside the timed events)",
+        "parallelism": f"replicas x{args.gpus} (frames sharded, no collective)",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (200 ms period)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except Exception:
+            pass
+    return 2070.0, "nominal maximum SM clock (recipe fallback)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.startswith("pa_bf"):
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "bf_fused_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_hash") != kernel_source_hash():
+            return None
+        return d.get(kind)
+    except Exception:
+        return None
+
+
+def ops_per_pair(k):
+    """Algorithmic FP32-pipe ops per (pixel, channel) pair for the combined
+    DAS + DMAS + DMAS-k pass (FMA = 1): floor/frac 2, lerp 2, root scale 1,
+    powers k-1, power sums k, plus DAS and the two DMAS sums (3)."""
+    if k == 1:
+        return 5 + 2  # DAS + the two DMAS sums
+    if k == 2:
+        return 2 * k + 4 + 1
+    return 2 * k + 7
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_run(wl, rf64_frames, k, budget_s):
+    """FP64 oracle over whole frames until ``budget_s`` is spent (>= 1 frame)."""
+    import oracle
+
+    pairs = wl["nx"] * wl["nz"] * wl["n_elem"]
+    t0 = time.perf_counter()
+    done = 0
+    for f in range(rf64_frames.shape[0]):
+        oracle.frame(wl, rf64_frames[f], order_k=k, stages=("raw", "env", "log"))
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, pairs * done / dt / 1e9, dt, oracle.get_threads()
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import synth
+
+    wl = workload()
+    frames = np.stack([synth.quantize(synth.make_frame(wl, 11, f), "f32")[1] for f in range(2)])
+    import oracle
+
+    oracle.build()
+    pairs = wl["nx"] * wl["nz"] * wl["n_elem"]
+    for _ in range(args.warmup):
+        oracle.frame(wl, frames[0], order_k=args.order)
+    ts = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.frame(wl, frames[s % 2], order_k=args.order)
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    value = pairs * args.steps / tot / 1e9
+    sample = (f"1 frame per step of the workload ({wl['nx']}x{wl['nz']} x {wl['n_elem']} ch, "
+              f"k={args.order}, raw+env+log), FP64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded cfg2 recipe)",
+        "config": config_dict(args, wl, {"frames_per_step": 1}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def precision_report(pa, wl, k, rf64, rf_dtype, comp):
+    """Error of one GPU frame against the FP64 oracle on the unquantised RF."""
+    import torch
+
+    import oracle
+    import synth
+
+    store, _ = synth.quantize(rf64[None], rf_dtype)
+    desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype=rf_dtype, compensated=comp)
+    with pa.Plan(desc) as plan:
+        if rf_dtype == "bf16":
+            t = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
+        else:
+            t = torch.from_numpy(store).cuda()
+        out = pa.beamform(plan, t, 7).cpu().numpy()[0]
+    ref = oracle.frame(wl, rf64, order_k=k)
+    rep = {}
+    for oi, o in enumerate(oracle.OUTPUT_ORDER):
+        r = ref["raw"][o]
+        e = ref["env"][o]
+        lg = ref["log"][o]
+        sel = lg >= -6.0
+        rep[o] = {
+            "raw_max_err_of_peak": float(np.max(np.abs(out[0, oi] - r)) / np.max(np.abs(r))),
+            "env_max_err_of_peak": float(np.max(np.abs(out[1, oi] - e)) / np.max(np.abs(e))),
+            "log_max_abs_db_top6db": float(np.max(np.abs(out[2, oi][sel] - lg[sel]))),
+            "log_mean_abs_db": float(np.mean(np.abs(out[2, oi] - lg))),
+        }
+    return rep
+
+
+def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
+    """Device-timed steps of one arithmetic form; returns (times_s, profile, plan_info)."""
+    import synth
+
+    F = frames64.shape[0]
+    store, _ = synth.quantize(frames64, rf_dtype)
+    if rf_dtype == "bf16":
+        rf = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
+    else:
+        rf = torch.from_numpy(store).cuda()
+    desc = pa.make_desc(wl, order_k=args.order, outputs=7, rf_dtype=rf_dtype, max_batch=F,
+                        compensated=comp)
+    plan = pa.Plan(desc, stream=stream)
+    stages = pa.PA_STAGE_LOG
+    out = torch.empty(plan.out_shape(F, stages), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush()
+            pa.beamform(plan, rf, stages, out=out, stream=stream)
+        stream.synchronize()
+        plan.profile_read()
+        plan.profile(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush()
+            evs[s][0].record(stream)
+            pa.beamform(plan, rf, stages, out=out, stream=stream)
+            evs[s][1].record(stream)
+        stream.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    times = [a.elapsed_time(b) / 1e3 for a, b in evs]
+    info = plan.info()
+    plan.close()
+    return times, prof, info
+
+
+def run_ours(args):
+    ws, rank, local, pg = dist_setup(args)
+    import torch
+
+    import synth
+    import paper_2203_14906_gb300 as pa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload()
+    F, k = args.frames, args.order
+    pairs_step = wl["nx"] * wl["nz"] * wl["n_elem"] * F
+    frames64 = np.stack([synth.make_frame(wl, 11, rank * F + f) for f in range(F)])
+    stream = torch.cuda.Stream(dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---- FP32 form (the headline)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    times, prof, info = time_form(pa, torch, wl, args, "f32", 0, frames64, stream, flush)
+    clocks = clk.stop()
+    barrier()
+    t_tot = sum(times)
+    if pg is not None:
+        t = torch.tensor([t_tot], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_tot = float(t.item())
+    value = pairs_step * ws * args.steps / t_tot / 1e9
+
+    # roofline of the dominant kernel (the fused beamformer)
+    bf_ms, bf_n = prof["bf_fused"]
+    bf_s = bf_ms / 1e3 / max(bf_n, 1)
+    opp = ops_per_pair(k)
+    achieved = info["active_pairs"] * F * opp / bf_s / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, mhz_src = sm_max_mhz()
+    peak = n_sm * 128 * mhz * 1e6 / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s (FP32 pipe, FMA=1)",
+        "frac": achieved / peak, "traffic": measured_traffic("dram_bytes_per_launch"),
+        "kernel": "k_bf_fused", "ops_per_pair": opp,
+        "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {mhz:g} MHz ({mhz_src})",
+        "kernel_ms_per_launch": bf_s * 1e3,
+        "share_of_step": bf_ms / (sum(v[0] for v in prof.values()) or 1),
+        "kernels_ms_per_launch": {kk: (v[0] / max(v[1], 1)) for kk, v in prof.items()},
+    }
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # ---- end to end through the host-buffer ABI call
+    desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype="f32", max_batch=F)
+    store, _ = synth.quantize(frames64, "f32")
+    rf_h = torch.from_numpy(store).pin_memory()
+    with pa.Plan(desc) as plan:
+        out_h = torch.empty(plan.out_shape(F, pa.PA_STAGE_LOG), dtype=torch.float32).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
+        barrier()
+        e2e_steps = max(1, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
+        te = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([te], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": pairs_step * ws * e2e_steps / te / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(rf_h.numel() * rf_h.element_size()),
+           "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size()),
+           "call": "pa_beamform_host (pinned host buffers)", "steps": e2e_steps}
+
+    extras = {}
+    if not args.no_extras:
+        # reduced-precision form on the same workload: BF16 RF + Kahan sums
+        t_bf, prof_bf, _ = time_form(pa, torch, wl, args, "bf16", 1, frames64, stream, flush)
+        v_bf = pairs_step * args.steps / sum(t_bf) / 1e9
+        extras["precision_form"] = {
+            "value": v_bf * ws, "unit": UNIT, "rf_dtype": "bf16", "compensated": True,
+            "vs_fp32_form": v_bf * ws / value,
+            "kernel_ms_per_launch": prof_bf["bf_fused"][0] / max(prof_bf["bf_fused"][1], 1),
+        }
+        if rank == 0:
+            extras["precision_report"] = {
+                "fp32": precision_report(pa, wl, k, frames64[0], "f32", 0),
+                "bf16_kahan": precision_report(pa, wl, k, frames64[0], "bf16", 1),
+                "against": "FP64 oracle on the unquantised RF, frame 0",
+            }
+            done, v_cpu, dt, cores = oracle_run(wl, frames64, k, args.cpu_seconds)
+            extras["cpu_baseline"] = {
+                "value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": (f"{done} whole frame(s) of the workload (raw+env+log, k={k}), "
+                           f"{dt:.1f} s, FP64, OpenMP over image columns"),
+            }
+    if not args.no_serving and rank == 0:
+        try:
+            from paper_2203_14906_gb300 import serving  # noqa: F401
+
+            extras["serving"] = serving.bench_summary()
+        except (ImportError, AttributeError):
+            extras["serving"] = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded point + line absorbers, 3% noise; cfg2 recipe)",
+            "config": config_dict(args, wl), "clocks": clocks, "e2e": e2e,
+            "gpu_launches": launches, "roofline": roofline,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

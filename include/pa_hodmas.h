@@ -166,6 +166,16 @@ pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
                            int32_t n_frames, float* out_host, uint32_t stages,
                            void* cuda_stream);
 
+/*
+ * Kernel timing.  While enabled, every launch of the plan's kernels is
+ * bracketed by CUDA events recorded on the stream it runs on (kernel kinds:
+ * 0 fused beamforming, 1 post-filter/envelope, 2 log compression).
+ * pa_plan_profile_read waits for the recorded events, returns the summed
+ * milliseconds and launch counts per kind and clears them.
+ */
+pa_status pa_plan_profile(pa_plan_t plan, int32_t enable);
+pa_status pa_plan_profile_read(pa_plan_t plan, double ms[3], int64_t launches[3]);
+
 /* Frees everything the plan owns after synchronising the streams it used.
  * NULL is accepted (no-op). */
 pa_status pa_destroy(pa_plan_t plan);

@@ -30,6 +30,8 @@ EXPORTS = (
     "pa_plan_get_info",
     "pa_beamform",
     "pa_beamform_host",
+    "pa_plan_profile",
+    "pa_plan_profile_read",
     "pa_destroy",
     "pa_status_str",
     "pa_last_error",
@@ -115,6 +117,11 @@ def load(checked: bool = False, build: bool = True):
         L.pa_beamform.restype = ctypes.c_int
         L.pa_beamform_host.argtypes = [vp, vp, i32, vp, u32, vp]
         L.pa_beamform_host.restype = ctypes.c_int
+        L.pa_plan_profile.argtypes = [vp, i32]
+        L.pa_plan_profile.restype = ctypes.c_int
+        L.pa_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64)]
+        L.pa_plan_profile_read.restype = ctypes.c_int
         L.pa_destroy.argtypes = [vp]
         L.pa_destroy.restype = ctypes.c_int
         L.pa_status_str.argtypes = [ctypes.c_int]
@@ -204,6 +211,17 @@ class Plan:
         """Host-pointer call (pa_beamform_host); returns when output is written."""
         check(self._L, self._L.pa_beamform_host(self._h, rf_host_ptr, int(n_frames), out_host_ptr,
                                                 int(stages), _stream_handle(stream)))
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around each of this plan's kernel launches."""
+        check(self._L, self._L.pa_plan_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel: (total_ms, launches)} since the last read; synchronises."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        check(self._L, self._L.pa_plan_profile_read(self._h, ms, n))
+        return {name: (ms[i], n[i]) for i, name in enumerate(("bf_fused", "post", "log"))}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

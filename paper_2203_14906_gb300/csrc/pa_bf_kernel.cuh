@@ -52,19 +52,19 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // Accumulator layout: [0] DAS = sum s, [1] q1 = sum sgn(s)|s|^(1/2),
 // [2] q2 = sum |s|, [3 + (m-1)] p_m = sum x^m for m = 1..k-1.  The last
 // power sum p_k is never accumulated: x^k = s for odd k (p_k = DAS) and
-// x^k = |s| for even k (p_k = q2).
+// x^k = |s| for even k (p_k = q2).  Every order accumulates DAS and DMAS.
 template <int K>
 struct NAcc {
-  static constexpr int value = (K == 1) ? 1 : (K == 2 ? 3 : K + 2);
+  static constexpr int value = (K <= 2) ? 3 : K + 2;
 };
 
 template <int K>
 __device__ __forceinline__ void pair_update(float* v, float s) {
   v[0] += s;
-  if constexpr (K >= 2) {
+  {
     const float as = fabsf(s);
     v[2] += as;
-    if constexpr (K == 2) {
+    if constexpr (K <= 2) {
       v[1] += copysignf(sqrt_approx(as), s);
     } else if constexpr (K == 3) {
       const float y = ex2_approx(lg2_approx(as) * (1.0f / 6.0f));  // |s|^(1/6)
@@ -110,13 +110,12 @@ template <int K>
 __device__ __forceinline__ void combine(const double* P, float& das, float& dmas,
                                         float& ho) {
   das = (float)P[0];
-  if constexpr (K == 1) {
-    dmas = 0.0f;
-    ho = das;
-  } else {
+  {
     const double dm = 0.5 * fma(P[1], P[1], -P[2]);  // Eq. 3
     dmas = (float)dm;
-    if constexpr (K == 2) {
+    if constexpr (K == 1) {
+      ho = das;
+    } else if constexpr (K == 2) {
       ho = dmas;
     } else {
       double p[K + 1];

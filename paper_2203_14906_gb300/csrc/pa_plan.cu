@@ -82,6 +82,10 @@ struct pa_plan_s {
   size_t h_rf_bytes = 0, h_out_bytes = 0;
   cudaStream_t hs[2] = {nullptr, nullptr};
   cudaEvent_t h_ev = nullptr;
+  // kernel timing (pa_plan_profile)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   // facts
   int64_t active_pairs = 0, executed_pairs = 0;
   size_t device_bytes = 0;
@@ -375,6 +379,15 @@ void free_plan(pa_plan_s* P) {
   for (int s = 0; s < 2; ++s)
     if (P->hs[s]) cudaStreamDestroy(P->hs[s]);
   if (P->h_ev) cudaEventDestroy(P->h_ev);
+  for (auto& e : P->ev_free) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : P->ev_used) {
+    cudaEventSynchronize(e.second.second);
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
   delete P;
 }
 
@@ -526,6 +539,31 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
 
 int stage_index(uint32_t stages, uint32_t stage) { return popcount3(stages & (stage - 1u)); }
 
+// Event pair around one kernel launch when timing is enabled.
+struct ProfScope {
+  pa_plan_s* P;
+  int kind;
+  cudaStream_t st;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  ProfScope(pa_plan_s* p, int k, cudaStream_t s) : P(p), kind(k), st(s) {
+    if (!P->prof) return;
+    if (!P->ev_free.empty()) {
+      ev = P->ev_free.back();
+      P->ev_free.pop_back();
+    } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
+               cudaEventCreate(&ev.second) != cudaSuccess) {
+      ev = {nullptr, nullptr};
+      return;
+    }
+    cudaEventRecord(ev.first, st);
+  }
+  ~ProfScope() {
+    if (!ev.first) return;
+    cudaEventRecord(ev.second, st);
+    P->ev_used.push_back({kind, ev});
+  }
+};
+
 // One launch sequence for nf <= max_batch frames.
 pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
                     cudaStream_t st, int* scratch) {
@@ -579,7 +617,10 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
   b.counter = scratch + 1;
   b.err = scratch;
   const int grid = std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms));
-  PA_CUDA(bf_launch(P->K, P->apod, P->comp, b, grid, P->threads, P->smem, st));
+  {
+    ProfScope ps(P, 0, st);
+    PA_CUDA(bf_launch(P->K, P->apod, P->comp, b, grid, P->threads, P->smem, st));
+  }
 
   if (stages & (PA_STAGE_ENV | PA_STAGE_LOG)) {
     PostParams q;
@@ -597,6 +638,7 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
     q.maxslot = scratch + 2;
     q.n_frames = nf;
     q.warps_per_block = P->post_wpb;
+    ProfScope ps(P, 1, st);
     PA_CUDA(post_launch(q, st));
   }
   if (stages & PA_STAGE_LOG) {
@@ -610,6 +652,7 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
     l.maxslot = scratch + 2;
     l.dyn_range_db = P->dyn_range;
     l.n_frames = nf;
+    ProfScope ps(P, 2, st);
     PA_CUDA(log_launch(l, P->num_sms, st));
   }
   return PA_OK;
@@ -803,6 +846,31 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   }
   PA_CUDA(cudaStreamSynchronize(P->hs[0]));
   PA_CUDA(cudaStreamSynchronize(P->hs[1]));
+  return PA_OK;
+}
+
+pa_status pa_plan_profile(pa_plan_t P, int32_t enable) {
+  if (!P) return fail(PA_EINVAL, "null plan");
+  P->prof = enable != 0;
+  return PA_OK;
+}
+
+pa_status pa_plan_profile_read(pa_plan_t P, double ms[3], int64_t launches[3]) {
+  if (!P || !ms || !launches) return fail(PA_EINVAL, "null argument");
+  DeviceGuard g(P->device);
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto& e : P->ev_used) {
+    PA_CUDA(cudaEventSynchronize(e.second.second));
+    float t = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&t, e.second.first, e.second.second));
+    ms[e.first] += t;
+    launches[e.first] += 1;
+    P->ev_free.push_back(e.second);
+  }
+  P->ev_used.clear();
   return PA_OK;
 }
 
