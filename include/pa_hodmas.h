@@ -180,6 +180,35 @@ pa_status pa_plan_profile_read(pa_plan_t plan, double ms[3], int64_t launches[3]
  * NULL is accepted (no-op). */
 pa_status pa_destroy(pa_plan_t plan);
 
+/*
+ * pa_log_compress_noalloc -- log compression (20 log10(env / image max),
+ * clipped to [-dyn_range_db, 0]; -dyn_range_db where env or the max is 0)
+ * of n_images envelope images that allocates no memory.  The paper has no
+ * counterpart: this is a deployment variant of the log stage for callers
+ * that cannot call cudaMalloc once streaming (e.g. a real-time acquisition
+ * loop that must not stall the device, or a host framework that owns all
+ * device memory); it needs no plan.
+ *   env_dev   [n_images][image_elems] FP32 envelopes (>= 0; negative values
+ *             count as 0), device memory, caller-owned, read only.
+ *   log_dev   [n_images][image_elems] FP32 output, caller-owned; may equal
+ *             env_dev (in place).
+ * The per-image maxima live in a fixed device array of PA_NOALLOC_MAX_IMAGES
+ * ints inside this library (16 KiB held on every GPU that loads it until the
+ * process exits); n_images > PA_NOALLOC_MAX_IMAGES returns PA_EINVAL.  The
+ * first call on a device looks up that array's device address (once per
+ * device), so make the first call before any stream capture.  Every call
+ * reuses the same array and clears the slots it needs on cuda_stream before
+ * use: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.  Asynchronous on
+ * cuda_stream.  No cudaMalloc, cudaFree or allocating library call is made.
+ * Errors: PA_EINVAL (sizes, null buffer), PA_ECUDA; pa_last_error() has the
+ * detail.
+ */
+#define PA_NOALLOC_MAX_IMAGES 4096
+pa_status pa_log_compress_noalloc(const float* env_dev, int32_t n_images,
+                                  int64_t image_elems, float dyn_range_db,
+                                  float* log_dev, void* cuda_stream);
+
 const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);

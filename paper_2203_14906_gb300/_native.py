@@ -122,6 +122,8 @@ def load(checked: bool = False, build: bool = True):
         L.pa_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
         L.pa_plan_profile_read.restype = ctypes.c_int
+        L.pa_log_compress_noalloc.argtypes = [vp, i32, ctypes.c_int64, ctypes.c_float, vp, vp]
+        L.pa_log_compress_noalloc.restype = ctypes.c_int
         L.pa_destroy.argtypes = [vp]
         L.pa_destroy.restype = ctypes.c_int
         L.pa_status_str.argtypes = [ctypes.c_int]

@@ -102,6 +102,9 @@ PA_DECLARE_ORDER(7)
 PA_DECLARE_ORDER(8)
 #undef PA_DECLARE_ORDER
 
+// Sets the thread-local message returned by pa_last_error().
+void set_error_message(const char* msg);
+
 cudaError_t post_configure(size_t smem);
 cudaError_t post_launch(const PostParams& p, cudaStream_t s);
 cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s);

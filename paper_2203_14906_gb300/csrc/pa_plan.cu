@@ -662,6 +662,8 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
 
 // ------------------------------------------------------------ dispatchers
 namespace pa {
+void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p, int grid, int block,
                       size_t smem, cudaStream_t s) {
   switch (order) {
