@@ -140,79 +140,84 @@ __device__ __forceinline__ void combine(const double* P, float& das, float& dmas
 }
 
 // ---- RF staging ---------------------------------------------------------
-__device__ __forceinline__ float rf_load(const BfParams& p, size_t idx) {
-  if (p.rf_dtype == PA_RF_F32) return __ldg(reinterpret_cast<const float*>(p.rf) + idx);
-  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p.rf) + idx);
-  if (p.rf_dtype == PA_RF_BF16) return __uint_as_float(((unsigned)u) << 16);
-  return __half2float(__ushort_as_half(u));
+// Samples are widened to FP32 on the way into shared memory; the storage type
+// only changes the load.
+template <int DT>
+__device__ __forceinline__ float rf_load(const void* rf, size_t idx) {
+  if constexpr (DT == PA_RF_F32) {
+    return __ldg(reinterpret_cast<const float*>(rf) + idx);
+  } else {
+    const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(rf) + idx);
+    if constexpr (DT == PA_RF_BF16) return __uint_as_float(((unsigned)u) << 16);
+    return __half2float(__ushort_as_half(u));
+  }
 }
 
-// Four consecutive samples at row + n (n % 4 == 0, row start aligned).
-__device__ __forceinline__ void rf_load4(const BfParams& p, size_t idx, float* r) {
-  if (p.rf_dtype == PA_RF_F32) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(p.rf) + idx));
+// Four consecutive samples at element idx (idx % 4 == 0, row start aligned).
+template <int DT>
+__device__ __forceinline__ void rf_load4(const void* rf, size_t idx, float* r) {
+  if constexpr (DT == PA_RF_F32) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(rf) + idx));
     r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
   } else {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(p.rf) + idx));
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(rf) + idx));
     const unsigned w[4] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      r[t] = (p.rf_dtype == PA_RF_BF16) ? __uint_as_float(w[t] << 16)
-                                        : __half2float(__ushort_as_half((unsigned short)w[t]));
+      if constexpr (DT == PA_RF_BF16) r[t] = __uint_as_float(w[t] << 16);
+      else r[t] = __half2float(__ushort_as_half((unsigned short)w[t]));
     }
   }
 }
 
+static_assert(kC == 4, "channel-base loads below read 2 x int4");
+
 // Stage the sample windows of virtual channels [v0, v0 + kNCS) of one tile.
-// Slot q of staged channel cv holds (r[lo+q], r[lo+q+1]); s_cb[cv] is the
-// shared-memory byte offset of sample 0 of that channel's window, so the
-// pair for sample n0 lives at s_cb[cv] + 8 n0.
-__device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int tile_id,
-                                            int v0, int* s_cb, unsigned char* smem,
-                                            int pairs_off) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+// Slot q of staged channel cv holds (r[n], r[n+1] - r[n]) for n = lo + q, so
+// the interpolated sample is one FMA, s = r[n] + a (r[n+1] - r[n]); samples
+// outside [0, Ns) (and virtual channels) are zero.  The plan-time table never
+// points a pair at a slot with exactly one tap inside the record, so a delay
+// whose taps leave the record reads (0, 0).  s_cb[cv] is the 32-bit shared
+// address of sample 0 of the channel's window, so the slot of sample n0 lives
+// at s_cb[cv] + 8 n0.  Work is spread over the whole block, four slots per
+// thread-iteration.
+template <int DT>
+__device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int tile_id, int v0,
+                                            int* s_cb, unsigned char* smem, uint32_t sbase) {
   const int W = p.window, W4 = W >> 2;
   const int ns = p.n_samples;
   const int* lo_t = p.lo + (size_t)tile_id * p.nv;
-  for (int cv = warp; cv < kNCS; cv += nwarps) {
+  const size_t frame_base = (size_t)frame * p.n_elem;
+  if (threadIdx.x < kNCS) {
+    const int v = v0 + threadIdx.x;
+    const int lo = v < p.nv ? __ldg(lo_t + v) : 0;
+    s_cb[threadIdx.x] = (int)sbase + kPairsOff + (int)threadIdx.x * W * 8 - lo * 8;
+  }
+  const int total = kNCS * W4;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
+    const int q = idx - cv * W4;
     const int v = v0 + cv;
     const int i = v + p.u0;
-    const bool in_v = v < p.nv;
-    const int lo = in_v ? __ldg(lo_t + v) : 0;
-    const int slot_off = pairs_off + cv * W * 8;
-    if (lane == 0) s_cb[cv] = slot_off - lo * 8;
-    float4* dst = reinterpret_cast<float4*>(smem + slot_off);
-    const bool real = in_v && i >= 0 && i < p.n_elem;
-    const size_t row = ((size_t)frame * p.n_elem + (real ? i : 0)) * (size_t)ns;
-    for (int q = lane; q < W4; q += 32) {
-      const int n = lo + 4 * q;
-      float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      bool all_valid = false;
-      if (real) {
-        if (p.vec_ok && n >= 0 && n + 4 <= ns - 1) {
-          rf_load4(p, row + n, r);
-          r[4] = rf_load(p, row + n + 4);
-          all_valid = true;
-        } else {
+    const bool real = v < p.nv && i >= 0 && i < p.n_elem;
+    const int n = (v < p.nv ? __ldg(lo_t + v) : 0) + 4 * q;
+    float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (real) {
+      const size_t row = (frame_base + i) * (size_t)ns;
+      if (p.vec_ok && n >= 0 && n + 4 <= ns - 1) {
+        rf_load4<DT>(p.rf, row + n, r);
+        r[4] = rf_load<DT>(p.rf, row + n + 4);
+      } else {
 #pragma unroll
-          for (int t = 0; t < 5; ++t) {
-            const int idx = n + t;
-            r[t] = (idx >= 0 && idx < ns) ? rf_load(p, row + idx) : 0.f;
-          }
+        for (int t = 0; t < 5; ++t) {
+          const int k = n + t;
+          if (k >= 0 && k < ns) r[t] = rf_load<DT>(p.rf, row + k);
         }
       }
-      float sx[4], sy[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int idx = n + t;
-        const bool ok = all_valid || (idx >= 0 && idx <= ns - 2);
-        sx[t] = ok ? r[t] : 0.f;
-        sy[t] = ok ? r[t + 1] : 0.f;
-      }
-      dst[2 * q] = make_float4(sx[0], sy[0], sx[1], sy[1]);
-      dst[2 * q + 1] = make_float4(sx[2], sy[2], sx[3], sy[3]);
     }
+    float4* dst = reinterpret_cast<float4*>(smem + kPairsOff + (size_t)(cv * W + 4 * q) * 8);
+    dst[0] = make_float4(r[0], r[1] - r[0], r[1], r[2] - r[1]);
+    dst[1] = make_float4(r[2], r[3] - r[2], r[3], r[4] - r[3]);
   }
 }
 
@@ -232,20 +237,29 @@ __device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC
   }
 }
 
+// Resident 256-thread blocks per SM the register allocation targets: three
+// (80 registers) for plain sums of orders <= 5, two for the larger accumulator
+// sets of compensated sums and orders >= 6.
+template <int K, bool COMP>
+struct MinBlocks {
+  static constexpr int value = (COMP || K >= 6) ? 2 : 3;
+};
+
 template <int K, bool APOD, bool COMP>
-__global__ void __launch_bounds__(256) k_bf_fused(const BfParams p) {
+__global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(const BfParams p) {
   constexpr int NA = NAcc<K>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_item = reinterpret_cast<int*>(smem);
   int* s_cb = reinterpret_cast<int*>(smem + 16);
-  const int pairs_off = 16 + ((kNCS * 4 + 15) & ~15);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const int pairs_off = (int)sbase + kPairsOff;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int per_tile = p.ngroups * p.n_frames;
   const int mstride = p.m * p.table_stride;
 #ifdef PA_CHECK_BOUNDS
-  const int smem_hi = pairs_off + kNCS * p.window * 8 - 8;
+  const int smem_hi = pairs_off + kNCS * p.window * 8 - 8;  // shared addresses
 #endif
 
   for (;;) {
@@ -289,51 +303,42 @@ __global__ void __launch_bounds__(256) k_bf_fused(const BfParams p) {
 
     for (int k = vk.x; k < vk.y; ++k) {
       __syncthreads();
-      stage_chunk(p, frame, tile_id, k * kNC, s_cb, smem, pairs_off);
+      if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+      else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+      else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
       __syncthreads();
       const int cu0 = p.u0 + k * kNC;
       int u = max(cu0, ur.x);
       const int u_end = min(cu0 + kNC, ur.y);
       if (u >= u_end) continue;
 
-      int2 e[kC];
-      float w[kC];
-      {
-        const int r0 = row_u0 - p.m * u;
+      // Table entries (n0, a) [and weight] of the kC steps starting at uu.
+      auto load_entries = [&](int2 (&ee)[kC], float (&ww)[kC], int uu) {
+        const int r0 = row_u0 - p.m * uu;
 #pragma unroll
         for (int tt = 0; tt < kC; ++tt) {
 #ifdef PA_CHECK_BOUNDS
           const int rr = r0 - tt * p.m;
           if (rr < 0 || rr >= p.ndrows) atomicOr(p.err, 1);
 #endif
-          e[tt] = __ldg(tcol + (r0 * p.table_stride - tt * mstride));
-          if constexpr (APOD) w[tt] = __ldg(wcol + (r0 * p.table_stride - tt * mstride));
+          ee[tt] = __ldg(tcol + (r0 * p.table_stride - tt * mstride));
+          if constexpr (APOD) ww[tt] = __ldg(wcol + (r0 * p.table_stride - tt * mstride));
         }
-      }
-      for (; u < u_end; u += kC) {
-        int cb[2 * kC - 1];
-        const int cvb = u - cu0;
-#pragma unroll
-        for (int q = 0; q < 2 * kC - 1; ++q) cb[q] = s_cb[cvb + q];
-        int2 en[kC];
-        float wn[kC];
-        const bool more = (u + kC < u_end);
-        if (more) {
-          const int r1 = row_u0 - p.m * (u + kC);
-#pragma unroll
-          for (int tt = 0; tt < kC; ++tt) {
-#ifdef PA_CHECK_BOUNDS
-            const int rr = r1 - tt * p.m;
-            if (rr < 0 || rr >= p.ndrows) atomicOr(p.err, 1);
-#endif
-            en[tt] = __ldg(tcol + (r1 * p.table_stride - tt * mstride));
-            if constexpr (APOD) wn[tt] = __ldg(wcol + (r1 * p.table_stride - tt * mstride));
-          }
+      };
+      // kC channel steps x kC columns = kC^2 pairs.
+      auto block = [&](const int2 (&ee)[kC], const float (&ww)[kC], int uu) {
+        int cb[2 * kC];
+        {
+          // channel bases of channels uu .. uu + 2kC - 2 (uu - cu0 is a multiple of 4)
+          const int4* cbv = reinterpret_cast<const int4*>(s_cb + (uu - cu0));
+          const int4 c0 = cbv[0], c1 = cbv[1];
+          cb[0] = c0.x; cb[1] = c0.y; cb[2] = c0.z; cb[3] = c0.w;
+          cb[4] = c1.x; cb[5] = c1.y; cb[6] = c1.z; cb[7] = c1.w;
         }
 #pragma unroll
         for (int tt = 0; tt < kC; ++tt) {
-          const int off = e[tt].x;
-          const float a = __int_as_float(e[tt].y);
+          const int off = ee[tt].x;
+          const float a = __int_as_float(ee[tt].y);
 #pragma unroll
           for (int c = 0; c < kC; ++c) {
             int addr = cb[tt + c] + off;
@@ -343,9 +348,10 @@ __global__ void __launch_bounds__(256) k_bf_fused(const BfParams p) {
               addr = pairs_off;
             }
 #endif
-            const float2 r = *reinterpret_cast<const float2*>(smem + addr);
-            float s = fmaf(a, r.y - r.x, r.x);
-            if constexpr (APOD) s *= w[tt];
+            float2 r;
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
+            float s = fmaf(a, r.y, r.x);
+            if constexpr (APOD) s *= ww[tt];
             pair_update<K>(acc[c], s);
           }
         }
@@ -355,13 +361,19 @@ __global__ void __launch_bounds__(256) k_bf_fused(const BfParams p) {
             fold = 0;
           }
         }
-        if (more) {
-#pragma unroll
-          for (int tt = 0; tt < kC; ++tt) {
-            e[tt] = en[tt];
-            if constexpr (APOD) w[tt] = wn[tt];
-          }
-        }
+      };
+      // Two blocks per iteration so the prefetched entries alternate between
+      // two register sets instead of being copied.
+      int2 ea[kC], eb[kC];
+      float wa[kC], wb[kC];
+      load_entries(ea, wa, u);
+      for (; u < u_end; u += 2 * kC) {
+        const bool has_b = u + kC < u_end;
+        if (has_b) load_entries(eb, wb, u + kC);
+        block(ea, wa, u);
+        if (!has_b) break;
+        if (u + 2 * kC < u_end) load_entries(ea, wa, u + 2 * kC);
+        block(eb, wb, u + kC);
       }
     }
     if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);

@@ -20,6 +20,10 @@ constexpr int kNCS = kNC + kC - 1;
 // Channel steps between Kahan folds of the compensated power sums.
 constexpr int kFoldBlocks = 2;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
+// Shared-memory layout of the fused kernel: 16 B work-item word, channel
+// bases (>= kNCS + 1 ints, multiple of 4), then the staged slots.
+constexpr int kCbInts = 40;
+constexpr int kPairsOff = 16 + kCbInts * 4;
 constexpr int kMaxThreads = 1024;
 
 // Parameters of the fused gather + interpolate + root + power-sum kernel.
@@ -44,6 +48,7 @@ struct BfParams {
   int nv;                 // virtual channels (zero rows pad both ends)
   int u0;                 // first channel step (= -(kC-1))
   int window;             // float2 slots staged per channel (multiple of 4)
+  int w4_inv;             // ceil(2^20 / (window / 4)): exact idx / (window / 4) by multiply-shift
   const int* lo;          // [n_tiles][nv] first staged sample per channel
   const int2* urange;     // [n_tiles][warps] channel-step range of a warp
   const int2* vchunks;    // [n_tiles] chunk range of a tile
@@ -64,7 +69,7 @@ struct PostParams {
   int n_out;           // outputs per stage
   int s_src, s_dst;    // stage index holding raw / receiving the envelope
   int nx, nz, m, log2m;
-  const float2* tw;    // [m/2] e^{-2 pi i k / m}
+  const float2* tw;    // [m] e^{-2 pi i k / m}
   const float* mask;   // [n_out][m] band-pass x analytic mask
   int* maxslot;        // [frames][n_out] float bits of the image maximum
   int n_frames;

@@ -96,7 +96,7 @@ namespace {
 
 // ---------------------------------------------------------- plan kernels
 struct TableGeom {
-  int ndrows, nzp, dmin;
+  int ndrows, nzp, dmin, ns;
   double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
   double dx, z0, dz, fs, c, t0, fnum;
 };
@@ -117,7 +117,13 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   const double lim = 1048576.0;
   if (fl < -lim) { fl = -lim; a = 0.0; }
   if (fl > lim) { fl = lim; a = 0.0; }
-  const int n0 = (int)fl;
+  int n0 = (int)fl;
+  // A delay whose taps leave the record contributes nothing (s = 0).  Staged
+  // samples outside [0, Ns) are zero, so pointing such delays at a slot whose
+  // two taps both lie outside the record gives s = 0 with no test per pair:
+  // n0 = -1 (taps -1, 0) moves to -2, n0 = Ns-1 (taps Ns-1, Ns) moves to Ns.
+  if (n0 == -1) n0 = -2;
+  if (n0 == g.ns - 1) n0 = g.ns;
   table[(size_t)row * g.nzp + z] = make_int2(n0 * 8, __float_as_int((float)a));
   if (wtab) {
     float w = 0.f;
@@ -298,7 +304,10 @@ void configure(pa_plan_s* P) {
   P->comp = d.compensated != 0;
   const double dx = (d.x1_m - d.x0_m) / d.nx;
   P->m = (int)std::lround(d.pitch_m / dx);
-  P->R = std::max(1, 4 / P->m);
+  // 32-column tiles halve the staged samples per pair; small images keep
+  // 16-column tiles so that there are enough tiles to fill the GPU.
+  const bool big = (int64_t)d.nx * d.nz >= 512 * 512;
+  P->R = std::max(1, (big ? 8 : 4) / P->m);
   P->slots = P->m * P->R;
   int B = 1;
   for (int b = 1; b <= 8; ++b)
@@ -327,7 +336,9 @@ void configure(pa_plan_s* P) {
     P->M <<= 1;
     ++P->log2M;
   }
-  P->post_wpb = std::max(1, std::min(8, (int)(65536 / (P->M * (int)sizeof(float2)))));
+  // twiddles + three M-point complex buffers per warp (two columns per warp)
+  P->post_wpb = std::max(
+      1, std::min(8, (int)(65536 / (3 * (P->M + P->M / 8) * (int)sizeof(float2)))));
   P->n_out = popcount3(d.outputs);
   int s = 0;
   for (int o = 0; o < 3; ++o) P->out_id[o] = (d.outputs >> o & 1u) ? s++ : -1;
@@ -342,7 +353,7 @@ size_t table_bytes(const pa_plan_s* P) {
   b += (size_t)P->n_tiles * P->nv * sizeof(int);
   b += (size_t)P->n_tiles * P->slots * sizeof(int2);
   b += (size_t)P->n_tiles * P->ngroups * sizeof(int2);
-  b += (size_t)(P->M / 2 + 1) * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
+  b += (size_t)P->M * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
   return b;
 }
 
@@ -402,17 +413,22 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   if ((s = dalloc(P, &P->lo, (size_t)P->n_tiles * P->nv)) != PA_OK) return s;
   if ((s = dalloc(P, &P->urange, (size_t)P->n_tiles * P->slots)) != PA_OK) return s;
   if ((s = dalloc(P, &P->vchunks, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
-  if ((s = dalloc(P, &P->tw, (size_t)P->M / 2 + 1)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->tw, (size_t)P->M)) != PA_OK) return s;
   if ((s = dalloc(P, &P->mask, (size_t)3 * P->M)) != PA_OK) return s;
   P->scratch_ints = 2 + (size_t)P->d.max_batch * 3;
   if ((s = dalloc(P, &P->scratch[0], P->scratch_ints)) != PA_OK) return s;
   PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
+
+  if ((size_t)36 * P->M > (size_t)200 * 1024)
+    return fail(PA_EUNSUPPORTED, "nz = %d needs a %d-point envelope FFT; at most 4096 is supported",
+                d.nz, P->M);
 
   // delay / apodisation table
   TableGeom tg;
   tg.ndrows = P->ndrows;
   tg.nzp = P->nz_pad;
   tg.dmin = P->dmin;
+  tg.ns = d.n_samples;
   tg.dx = (d.x1_m - d.x0_m) / d.nx;
   tg.x_const = d.x0_m + 0.5 * (d.n_elem - 1) * d.pitch_m;
   tg.z0 = d.z0_m;
@@ -504,8 +520,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
                           st));
 
   // shared memory and occupancy of the fused kernel
-  const size_t pairs_off = 16 + ((kNCS * 4 + 15) & ~15);
-  P->smem = pairs_off + (size_t)kNCS * P->window * sizeof(float2);
+  P->smem = kPairsOff + (size_t)kNCS * P->window * sizeof(float2);
   if (P->smem > 200 * 1024)
     return fail(PA_EUNSUPPORTED,
                 "RF window of %d samples per channel needs %zu B of shared memory; use a finer "
@@ -517,8 +532,8 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
                 P->threads, P->smem);
 
   // post-filter tables (host FP64 -> FP32)
-  std::vector<float2> tw((size_t)P->M / 2 + 1);
-  for (int k = 0; k <= P->M / 2; ++k) {
+  std::vector<float2> tw((size_t)P->M);
+  for (int k = 0; k < P->M; ++k) {
     const double ang = -2.0 * M_PI * (double)k / (double)P->M;
     tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
@@ -532,7 +547,8 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   PA_CUDA(cudaMemcpyAsync(P->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
   PA_CUDA(cudaMemcpyAsync(P->mask, mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice,
                           st));
-  PA_CUDA(post_configure(65536));  // the largest any plan uses (post_wpb * M * 8 <= 64 KiB)
+  // post kernel: (3 post_wpb (M + M/8) + M) * 8 bytes, at most 200 KiB
+  PA_CUDA(post_configure((size_t)200 * 1024));
   PA_CUDA(cudaStreamSynchronize(st));
   return PA_OK;
 }
@@ -602,6 +618,7 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
   b.nv = P->nv;
   b.u0 = P->u0;
   b.window = P->window;
+  b.w4_inv = (int)(((1u << 20) + (unsigned)(P->window / 4) - 1) / (unsigned)(P->window / 4));
   b.lo = P->lo;
   b.urange = P->urange;
   b.vchunks = P->vchunks;

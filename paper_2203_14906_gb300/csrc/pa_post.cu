@@ -2,97 +2,262 @@
 // the beamformed images are band-pass filtered, envelope-detected through
 // the Hilbert transform and log-compressed before display).
 //
-// k_post: one warp per depth column.  The column is zero-padded to
-// M = 2^ceil(log2 nz) in shared memory, transformed by a radix-2
-// decimation-in-time FFT (bit-reversed load, natural-order spectrum),
-// multiplied by the plan's real mask H = band-pass x analytic weights
-// (1 at DC and M/2, 2 on positive bins, 0 on negative bins), and
-// transformed back by a decimation-in-frequency inverse FFT (natural
-// input, bit-reversed output).  The envelope |y[z]| / M for z < nz is
-// written and the column maximum is merged into the image maximum with an
-// atomic max on the float bits (the envelope is non-negative).  The column
-// is read completely before it is written, so source and destination may
-// be the same plane.
+// k_post: one warp per pair of depth columns (j, j+1).  The two real columns
+// are packed into one complex sequence a + i b, zero-padded to
+// M = 2^ceil(log2 nz) and transformed by a Stockham (self-sorting) FFT with
+// radix-8 passes (radix 4 / 2 for the remainder), each pass keeping its
+// butterflies in registers.  The two spectra are separated with the
+// conjugate symmetry of real inputs, A[k] = (Z[k] + Z*[M-k]) / 2 and
+// B[k] = (Z[k] - Z*[M-k]) / (2i), multiplied by the plan's real mask H
+// (band-pass x analytic weights: 1 at DC and M/2, 2 on positive bins, 0 on
+// negative bins) and conjugated; a forward FFT of conj(H A) is the complex
+// conjugate of M IFFT(H A), so the envelope is |FFT(conj(H A))[z]| / M.  The
+// column maximum is merged into the image maximum with an atomic max on the
+// float bits (the envelope is non-negative).  Columns are read completely
+// before anything is written, so source and destination may be one plane.
 //
 // k_log: 20 log10(env / image max), clipped to [-DR, 0]; elementwise.
 #include "pa_internal.cuh"
 
 namespace pa {
 
-__device__ __forceinline__ int bit_reverse(int n, int log2m) {
-  return log2m == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - log2m));
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// In-register forward DFT of R = 2, 4 or 8 points (decimation in frequency,
+// then the bit-reversed results are put back in natural order).
+template <int R>
+__device__ __forceinline__ void dft_regs(float2 (&x)[R]) {
+  if constexpr (R == 2) {
+    const float2 a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    float2 t0 = cadd(x[0], x[2]), t2 = csub(x[0], x[2]);
+    float2 t1 = cadd(x[1], x[3]), t3 = cmul_mi(csub(x[1], x[3]));
+    x[0] = cadd(t0, t1);
+    x[2] = csub(t0, t1);
+    x[1] = cadd(t2, t3);
+    x[3] = csub(t2, t3);
+  } else {
+    const float h = 0.70710678118654752f;
+    float2 y[8];
+    // span 4
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      y[n] = cadd(x[n], x[n + 4]);
+      y[n + 4] = csub(x[n], x[n + 4]);
+    }
+    y[5] = make_float2(h * (y[5].x + y[5].y), h * (y[5].y - y[5].x));     // * e^{-i pi/4}
+    y[6] = cmul_mi(y[6]);                                                // * e^{-i pi/2}
+    y[7] = make_float2(h * (y[7].y - y[7].x), -h * (y[7].x + y[7].y));    // * e^{-3i pi/4}
+    // span 2
+    float2 z[8];
+#pragma unroll
+    for (int b = 0; b < 8; b += 4) {
+      z[b] = cadd(y[b], y[b + 2]);
+      z[b + 2] = csub(y[b], y[b + 2]);
+      z[b + 1] = cadd(y[b + 1], y[b + 3]);
+      z[b + 3] = cmul_mi(csub(y[b + 1], y[b + 3]));
+    }
+    // span 1, outputs in bit-reversed positions
+    x[0] = cadd(z[0], z[1]);
+    x[4] = csub(z[0], z[1]);
+    x[2] = cadd(z[2], z[3]);
+    x[6] = csub(z[2], z[3]);
+    x[1] = cadd(z[4], z[5]);
+    x[5] = csub(z[4], z[5]);
+    x[3] = cadd(z[6], z[7]);
+    x[7] = csub(z[6], z[7]);
+  }
 }
 
+// Shared buffers hold element i at i + i/8: one padding slot every eight
+// elements keeps the strided stores of the first passes (stride R elements)
+// free of multi-way bank conflicts.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+
+// Twiddles W^(r k) for r = 1..R-1 from three table reads (W^k, W^2k, W^4k)
+// and products of them.
+template <int R>
+__device__ __forceinline__ void twiddles(const float2* tw, int m, int idx, float2 (&w)[R]) {
+  w[1] = tw[idx];
+  if constexpr (R >= 4) {
+    w[2] = tw[(2 * idx) & (m - 1)];
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R == 8) {
+    w[4] = tw[(4 * idx) & (m - 1)];
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+  }
+}
+
+// One Stockham pass of radix R over sub-transforms of length ns.
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int m, int ns,
+                                              const float2* tw, int lane) {
+  const int groups = m / R;
+  const int tw_step = m / (ns * R);
+  for (int j = lane; j < groups; j += 32) {
+    const int k = j & (ns - 1);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = in[pidx(j + r * groups)];
+    if (ns > 1) {
+      float2 w[R];
+      twiddles<R>(tw, m, k * tw_step, w);
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
+    }
+    dft_regs<R>(x);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[pidx(base + r * ns)] = x[r];
+  }
+}
+
+// Forward FFT of buf_a; returns the buffer (buf_a or buf_b) holding the result.
+__device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, const float2* tw,
+                               int lane) {
+  // tw: shared-memory copy of e^{-2 pi i k / m}, k < m
+  float2* in = buf_a;
+  float2* out = buf_b;
+  int ns = 1, rem = log2m;
+  while (rem > 0) {
+    if (rem >= 3) {
+      stockham_pass<8>(in, out, m, ns, tw, lane);
+      ns *= 8;
+      rem -= 3;
+    } else if (rem == 2) {
+      stockham_pass<4>(in, out, m, ns, tw, lane);
+      ns *= 4;
+      rem -= 2;
+    } else {
+      stockham_pass<2>(in, out, m, ns, tw, lane);
+      ns *= 2;
+      rem -= 1;
+    }
+    __syncwarp();
+    float2* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+// Shared memory: the M-entry twiddle table, then three M-point complex
+// buffers per warp.
 __global__ void __launch_bounds__(256) k_post(const PostParams p) {
   extern __shared__ __align__(16) float2 sbuf[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.x * p.warps_per_block + warp;
+  const int M = p.m;
+  const int MP = M + (M >> 3);  // padded buffer length
+  float2* tw = sbuf;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) tw[k] = __ldg(p.tw + k);
+  __syncthreads();
+  const int j0 = 2 * (blockIdx.x * p.warps_per_block + warp);
   const int o = blockIdx.y, f = blockIdx.z;
-  if (j >= p.nx) return;  // warps are independent: no block barrier below
-  const int M = p.m, L = p.log2m, half = M >> 1;
-  float2* buf = sbuf + (size_t)warp * M;
+  if (j0 >= p.nx) return;  // no block barrier below
+  const bool two = j0 + 1 < p.nx;
+  float2* b0 = sbuf + M + (size_t)warp * 3 * MP;
+  float2* b1 = b0 + MP;
+  float2* b2 = b1 + MP;
   const size_t plane = (size_t)p.nx * p.nz;
   const float* src = p.out + ((size_t)f * p.planes + (size_t)p.s_src * p.n_out + o) * plane +
-                     (size_t)j * p.nz;
+                     (size_t)j0 * p.nz;
   float* dst = p.out + ((size_t)f * p.planes + (size_t)p.s_dst * p.n_out + o) * plane +
-               (size_t)j * p.nz;
+               (size_t)j0 * p.nz;
+  const bool vec = (p.nz & 3) == 0;  // column starts 16-byte aligned
 
-  for (int n = lane; n < M; n += 32) {
-    const float x = (n < p.nz) ? src[n] : 0.f;
-    buf[bit_reverse(n, L)] = make_float2(x, 0.f);
+  if (vec) {
+    for (int n = 4 * lane; n < M; n += 128) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (n < p.nz) {
+        a = *reinterpret_cast<const float4*>(src + n);
+        if (two) b = *reinterpret_cast<const float4*>(src + p.nz + n);
+      }
+      b0[pidx(n)] = make_float2(a.x, b.x);
+      b0[pidx(n + 1)] = make_float2(a.y, b.y);
+      b0[pidx(n + 2)] = make_float2(a.z, b.z);
+      b0[pidx(n + 3)] = make_float2(a.w, b.w);
+    }
+  } else {
+    for (int n = lane; n < M; n += 32) {
+      const bool in_col = n < p.nz;
+      const float a = in_col ? src[n] : 0.f;
+      const float b = (in_col && two) ? src[p.nz + n] : 0.f;
+      b0[pidx(n)] = make_float2(a, b);
+    }
   }
   __syncwarp();
+  float2* Z = fft_forward(b0, b1, M, p.log2m, tw, lane);
+  float2* F = (Z == b0) ? b1 : b0;  // free buffer
 
-  // forward DIT, butterfly span h = 1, 2, ..., M/2; twiddle e^{-2 pi i pos/(2h)}
-  for (int h = 1, tws = half; h < M; h <<= 1, tws >>= 1) {
-    for (int b = lane; b < half; b += 32) {
-      const int pos = b & (h - 1);
-      const int i0 = ((b - pos) << 1) + pos;
-      const int i1 = i0 + h;
-      const float2 w = __ldg(p.tw + pos * tws);
-      const float2 a = buf[i0], c = buf[i1];
-      const float tr = c.x * w.x - c.y * w.y;
-      const float ti = c.x * w.y + c.y * w.x;
-      buf[i0] = make_float2(a.x + tr, a.y + ti);
-      buf[i1] = make_float2(a.x - tr, a.y - ti);
-    }
-    __syncwarp();
-  }
-
+  // Split the packed spectrum and apply the mask.  Bins k and M-k are handled
+  // by the same lane, so conj(H B) can overwrite Z in place; conj(H A) goes
+  // to b2.  H vanishes above M/2.
   const float* mk = p.mask + (size_t)o * M;
-  for (int b = lane; b < M; b += 32) {
-    const float hb = __ldg(mk + b);
-    const float2 v = buf[b];
-    buf[b] = make_float2(v.x * hb, v.y * hb);
+  const int half = M >> 1;
+  for (int k = lane; k <= half; k += 32) {
+    const int km = (M - k) & (M - 1);
+    const float2 z = Z[pidx(k)], zc = Z[pidx(km)];
+    const float hk = 0.5f * __ldg(mk + k);
+    // A[k] = (z + conj zc) / 2,  B[k] = (z - conj zc) / (2i)
+    b2[pidx(k)] = make_float2(hk * (z.x + zc.x), -hk * (z.y - zc.y));
+    Z[pidx(k)] = make_float2(hk * (z.y + zc.y), hk * (z.x - zc.x));
+    if (km != k) {
+      const float hm = 0.5f * __ldg(mk + km);  // zero for km > M/2
+      b2[pidx(km)] = make_float2(hm * (zc.x + z.x), -hm * (zc.y - z.y));
+      Z[pidx(km)] = make_float2(hm * (zc.y + z.y), hm * (zc.x - z.x));
+    }
   }
   __syncwarp();
-
-  // inverse DIF, span h = M/2, ..., 1; twiddle e^{+2 pi i pos/(2h)}
-  for (int h = half, tws = 1; h >= 1; h >>= 1, tws <<= 1) {
-    for (int b = lane; b < half; b += 32) {
-      const int pos = b & (h - 1);
-      const int i0 = ((b - pos) << 1) + pos;
-      const int i1 = i0 + h;
-      const float2 w = __ldg(p.tw + pos * tws);
-      const float2 a = buf[i0], c = buf[i1];
-      buf[i0] = make_float2(a.x + c.x, a.y + c.y);
-      const float dx = a.x - c.x, dy = a.y - c.y;
-      buf[i1] = make_float2(dx * w.x + dy * w.y, dy * w.x - dx * w.y);
-    }
-    __syncwarp();
-  }
-
   const float inv_m = 1.0f / (float)M;
+  const float2* Ya = fft_forward(b2, F, M, p.log2m, tw, lane);
   float mx = 0.f;
-  for (int n = lane; n < p.nz; n += 32) {
-    const float2 y = buf[bit_reverse(n, L)];
-    const float env = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
-    dst[n] = env;
-    mx = fmaxf(mx, env);
+  auto emit = [&](const float2* Y, float* col) {
+    if (vec) {
+      for (int n = 4 * lane; n < p.nz; n += 128) {
+        float e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float2 y = Y[pidx(n + t)];
+          e[t] = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
+          mx = fmaxf(mx, e[t]);
+        }
+        *reinterpret_cast<float4*>(col + n) = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    } else {
+      for (int n = lane; n < p.nz; n += 32) {
+        const float2 y = Y[pidx(n)];
+        const float env = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
+        col[n] = env;
+        mx = fmaxf(mx, env);
+      }
+    }
+  };
+  emit(Ya, dst);
+  if (two) {
+    __syncwarp();
+    // Ya lives in b2 or F; the FFT of the B half ping-pongs between Z and the
+    // buffer Ya does not use.
+    float2* G = (Ya == b2) ? F : b2;
+    emit(fft_forward(Z, G, M, p.log2m, tw, lane), dst + p.nz);
   }
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
   if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
+}
+
+__device__ __forceinline__ float log_db(float env, float mx, float inv, float dr) {
+  return (mx > 0.f && env > 0.f) ? fminf(0.f, fmaxf(-dr, 20.0f * log10f(env * inv))) : -dr;
 }
 
 __global__ void __launch_bounds__(256) k_log(const LogParams p) {
@@ -103,12 +268,19 @@ __global__ void __launch_bounds__(256) k_log(const LogParams p) {
   const float dr = p.dyn_range_db;
   const float* src = p.out + ((size_t)f * p.planes + (size_t)p.s_src * p.n_out + o) * p.plane_elems;
   float* dst = p.out + ((size_t)f * p.planes + (size_t)p.s_dst * p.n_out + o) * p.plane_elems;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < p.plane_elems;
-       q += (long long)gridDim.x * blockDim.x) {
-    const float env = src[q];
-    float v = -dr;
-    if (mx > 0.f && env > 0.f) v = fminf(0.f, fmaxf(-dr, 20.0f * log10f(env * inv)));
-    dst[q] = v;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((p.plane_elems & 3) == 0) {  // planes start 16-byte aligned
+    const long long n4 = p.plane_elems >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (long long q = t0; q < n4; q += stride) {
+      const float4 e = s4[q];
+      d4[q] = make_float4(log_db(e.x, mx, inv, dr), log_db(e.y, mx, inv, dr),
+                          log_db(e.z, mx, inv, dr), log_db(e.w, mx, inv, dr));
+    }
+  } else {
+    for (long long q = t0; q < p.plane_elems; q += stride) dst[q] = log_db(src[q], mx, inv, dr);
   }
 }
 
@@ -117,16 +289,18 @@ cudaError_t post_configure(size_t smem) {
 }
 
 cudaError_t post_launch(const PostParams& p, cudaStream_t s) {
-  const size_t smem = (size_t)p.warps_per_block * p.m * sizeof(float2);
-  dim3 grid((p.nx + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
+  const size_t mp = (size_t)p.m + (p.m >> 3);
+  const size_t smem = ((size_t)p.warps_per_block * 3 * mp + p.m) * sizeof(float2);
+  const int col_pairs = (p.nx + 1) / 2;
+  dim3 grid((col_pairs + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
   k_post<<<grid, p.warps_per_block * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s) {
-  long long blocks = (p.plane_elems + 255) / 256;
+  long long blocks = (p.plane_elems / 4 + 255) / 256 + 1;
   const long long images = (long long)p.n_frames * p.n_out;
-  const long long target = (long long)num_sms * 8;
+  const long long target = (long long)num_sms * 32;
   long long per_img = (target + images - 1) / images;
   if (per_img < 1) per_img = 1;
   if (blocks > per_img) blocks = per_img;
