@@ -167,6 +167,16 @@ pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
                            void* cuda_stream);
 
 /*
+ * Launch mode.  By default (enable = 1) each pa_beamform launch sequence
+ * (clear, fused beamforming kernel, post-filter, log) runs as one CUDA graph;
+ * the plan keeps one executable graph per (frames per launch, stages) and
+ * only rewrites its buffer pointers on later calls.  enable = 0 launches the
+ * kernels one by one.  Results are identical either way.  While kernel
+ * timing is on (pa_plan_profile) kernels are launched one by one.
+ */
+pa_status pa_plan_use_graph(pa_plan_t plan, int32_t enable);
+
+/*
  * Kernel timing.  While enabled, every launch of the plan's kernels is
  * bracketed by CUDA events recorded on the stream it runs on (kernel kinds:
  * 0 fused beamforming, 1 post-filter/envelope, 2 log compression).
@@ -175,6 +185,77 @@ pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
  */
 pa_status pa_plan_profile(pa_plan_t plan, int32_t enable);
 pa_status pa_plan_profile_read(pa_plan_t plan, double ms[3], int64_t launches[3]);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of beamforming requests (not in the paper;
+ * it serves the paper's real-time use, Section 5, with many concurrent
+ * frames of different geometries and orders).
+ *
+ * A server owns a scheduler thread, a cache of resident plans (delay tables
+ * stay on the device between requests) and `slots` CUDA streams.  Each
+ * request brings one RF frame in host memory and receives its output images
+ * in host memory.  Whenever a slot is free the scheduler takes the oldest
+ * request that has arrived, adds up to max_batch - 1 later arrivals with the
+ * same descriptor, and runs them as one batch: RF copies, pa_beamform,
+ * output copies, all on the slot's stream, so batches of different
+ * requests overlap on the device.  A batch is admitted only when the device
+ * memory it needs (its RF and output buffers, plus a new plan's tables) fits
+ * in device_budget_bytes next to what is in flight; otherwise it waits.
+ * Frames are independent and each pixel's arithmetic is fixed, so a result
+ * is the same whichever batch it ran in.
+ * ---------------------------------------------------------------------- */
+typedef struct pa_server_s* pa_server_t;
+
+typedef struct {
+  size_t device_budget_bytes; /* admission limit: plans + in-flight buffers   */
+  int32_t slots;              /* concurrent batches (streams), >= 1           */
+  int32_t max_batch;          /* frames per batch, >= 1                       */
+  int32_t max_plans;          /* resident plans kept (least recently used
+                                 idle plans are destroyed beyond this)        */
+  uint32_t stages;            /* PA_STAGE_* written for every request         */
+} pa_server_config;
+
+typedef struct {
+  uint64_t ticket;
+  pa_status status;           /* PA_OK, or why the request failed            */
+  double arrival_s;           /* request arrival, seconds on the server clock */
+  double start_s;             /* its batch was issued                          */
+  double done_s;              /* the scheduler saw its batch complete          */
+  double latency_ms;          /* done_s - arrival_s                            */
+  int32_t batch_frames;       /* frames in its batch                           */
+} pa_request_result;
+
+typedef struct {
+  uint64_t submitted, completed, failed, batches;
+  size_t bytes_in_use, bytes_peak;   /* admission accounting                 */
+  int32_t plans_resident;
+} pa_server_stats;
+
+/* Starts the scheduler thread on the current CUDA device.  The server clock
+ * (seconds) starts at 0 here. */
+pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out);
+/* Current server-clock time in seconds. */
+double pa_server_now(pa_server_t srv);
+/*
+ * Queue one frame.  rf_host: [N][Ns] in desc->rf_dtype; out_host: [n_stages]
+ * [n_outputs][nx][nz] FP32; both stay caller-owned and must stay valid until
+ * the request completes (pinned memory gives full copy speed).  arrival_s:
+ * server-clock time at which the request becomes visible to the scheduler
+ * (<= now: immediately; later values replay a recorded arrival trace).
+ * desc->max_batch is ignored (the server's max_batch applies).
+ * Errors: PA_EINVAL (descriptor or pointers), PA_ENOMEM (one frame alone
+ * needs more than the budget).  The call never blocks on the device.
+ */
+pa_status pa_server_submit(pa_server_t srv, const pa_plan_desc* desc, const void* rf_host,
+                           float* out_host, double arrival_s, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request; PA_ETIMEOUT if it is
+ * still pending.  A finished request's result can be read once. */
+pa_status pa_server_wait(pa_server_t srv, uint64_t ticket, int32_t timeout_ms,
+                         pa_request_result* result);
+pa_status pa_server_get_stats(pa_server_t srv, pa_server_stats* stats);
+/* Waits for in-flight batches, stops the thread and frees every plan and
+ * buffer.  Pending requests that never ran complete with PA_EBUSY. */
+pa_status pa_server_destroy(pa_server_t srv);
 
 /* Frees everything the plan owns after synchronising the streams it used.
  * NULL is accepted (no-op). */

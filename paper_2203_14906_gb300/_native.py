@@ -30,6 +30,7 @@ EXPORTS = (
     "pa_plan_get_info",
     "pa_beamform",
     "pa_beamform_host",
+    "pa_plan_use_graph",
     "pa_plan_profile",
     "pa_plan_profile_read",
     "pa_destroy",
@@ -117,6 +118,8 @@ def load(checked: bool = False, build: bool = True):
         L.pa_beamform.restype = ctypes.c_int
         L.pa_beamform_host.argtypes = [vp, vp, i32, vp, u32, vp]
         L.pa_beamform_host.restype = ctypes.c_int
+        L.pa_plan_use_graph.argtypes = [vp, i32]
+        L.pa_plan_use_graph.restype = ctypes.c_int
         L.pa_plan_profile.argtypes = [vp, i32]
         L.pa_plan_profile.restype = ctypes.c_int
         L.pa_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -213,6 +216,10 @@ class Plan:
         """Host-pointer call (pa_beamform_host); returns when output is written."""
         check(self._L, self._L.pa_beamform_host(self._h, rf_host_ptr, int(n_frames), out_host_ptr,
                                                 int(stages), _stream_handle(stream)))
+
+    def use_graph(self, enable: bool = True):
+        """Launch each sequence as a CUDA graph (default) or kernel by kernel."""
+        check(self._L, self._L.pa_plan_use_graph(self._h, int(bool(enable))))
 
     def profile(self, enable: bool = True):
         """Record CUDA events around each of this plan's kernel launches."""

@@ -429,4 +429,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(c
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f,      \
                                                          block, smem);          \
   }                                                                             \
+  const void* bf_func_k##K(bool apod, bool comp) {                              \
+    return reinterpret_cast<const void*>(pick_k##K(apod, comp));                \
+  }                                                                             \
   }

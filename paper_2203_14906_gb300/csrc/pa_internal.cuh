@@ -85,6 +85,17 @@ struct LogParams {
   int n_frames;
 };
 
+// A kernel launch described as data (direct launch or CUDA-graph node).
+struct LaunchSpec {
+  const void* func = nullptr;
+  dim3 grid, block;
+  size_t smem = 0;
+};
+
+const void* bf_func(int order, bool apod, bool comp);
+void post_spec(const PostParams& p, LaunchSpec* s);
+void log_spec(const LogParams& p, int num_sms, LaunchSpec* s);
+
 // Launchers (one translation unit per order keeps the builds parallel).
 cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p,
                       int grid, int block, size_t smem, cudaStream_t s);
@@ -96,7 +107,8 @@ cudaError_t bf_occupancy(int order, bool apod, bool comp, int block,
                              int grid, int block, size_t smem,              \
                              cudaStream_t s);                               \
   cudaError_t bf_occupancy_k##K(bool apod, bool comp, int block,            \
-                                size_t smem, int* blocks_per_sm);
+                                size_t smem, int* blocks_per_sm);           \
+  const void* bf_func_k##K(bool apod, bool comp);
 PA_DECLARE_ORDER(1)
 PA_DECLARE_ORDER(2)
 PA_DECLARE_ORDER(3)

@@ -82,6 +82,17 @@ struct pa_plan_s {
   size_t h_rf_bytes = 0, h_out_bytes = 0;
   cudaStream_t hs[2] = {nullptr, nullptr};
   cudaEvent_t h_ev = nullptr;
+  // CUDA graphs of the launch sequence, one per (frames, stages)
+  struct GraphEntry {
+    int nf = 0;
+    uint32_t stages = 0;
+    cudaGraph_t graph = nullptr;  // kept alive: exec-node updates name its nodes
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_memset = nullptr;  // clearing kernel
+    cudaGraphNode_t n_bf = nullptr, n_post = nullptr, n_log = nullptr;
+  };
+  std::vector<GraphEntry> graphs;
+  bool use_graph = true;
   // kernel timing (pa_plan_profile)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
@@ -198,6 +209,11 @@ __global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wt
     }
   }
   urange[(size_t)tile * slots + sl] = r;
+}
+
+// Clears the work counter and image maxima before a launch sequence.
+__global__ void k_zero_ints(int* p, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
 }
 
 // Pairs with a non-zero apodisation weight (for the active-pair rate).
@@ -390,6 +406,10 @@ void free_plan(pa_plan_s* P) {
   for (int s = 0; s < 2; ++s)
     if (P->hs[s]) cudaStreamDestroy(P->hs[s]);
   if (P->h_ev) cudaEventDestroy(P->h_ev);
+  for (auto& g : P->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
   for (auto& e : P->ev_free) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -580,9 +600,19 @@ struct ProfScope {
   }
 };
 
-// One launch sequence for nf <= max_batch frames.
-pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
-                    cudaStream_t st, int* scratch) {
+// Parameters of the launches of one chunk of nf <= max_batch frames.
+struct ChunkLaunch {
+  BfParams b;
+  PostParams q;
+  LogParams l;
+  LaunchSpec sb, sq, sl;
+  bool post = false, log = false;
+  int* zero = nullptr;  // counter + image maxima, cleared before the kernels
+  size_t zero_ints = 0;
+};
+
+void prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                   int* scratch, ChunkLaunch* c) {
   const pa_plan_desc& d = P->d;
   const int n_st = popcount3(stages);
   const int planes = n_st * P->n_out;
@@ -591,10 +621,10 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
   const uint32_t env_stage = (stages & PA_STAGE_ENV) ? PA_STAGE_ENV : PA_STAGE_LOG;
   const int s_raw = stage_index(stages, raw_stage);
   const int s_env = stage_index(stages, env_stage);
+  c->zero = scratch + 1;
+  c->zero_ints = 1 + (size_t)nf * P->n_out;
 
-  PA_CUDA(cudaMemsetAsync(scratch + 1, 0, (1 + (size_t)nf * P->n_out) * sizeof(int), st));
-
-  BfParams b;
+  BfParams& b = c->b;
   b.rf = rf;
   b.rf_dtype = (int)d.rf_dtype;
   b.vec_ok = (d.n_samples % 4) == 0;
@@ -633,46 +663,137 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
   b.n_items = P->n_tiles * P->ngroups * nf;
   b.counter = scratch + 1;
   b.err = scratch;
-  const int grid = std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms));
+  c->sb.func = bf_func(P->K, P->apod, P->comp);
+  c->sb.grid = dim3(std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms)));
+  c->sb.block = dim3(P->threads);
+  c->sb.smem = P->smem;
+
+  c->post = (stages & (PA_STAGE_ENV | PA_STAGE_LOG)) != 0;
+  c->log = (stages & PA_STAGE_LOG) != 0;
+  PostParams& q = c->q;
+  q.out = out;
+  q.planes = planes;
+  q.n_out = P->n_out;
+  q.s_src = s_raw;
+  q.s_dst = s_env;
+  q.nx = d.nx;
+  q.nz = d.nz;
+  q.m = P->M;
+  q.log2m = P->log2M;
+  q.tw = P->tw;
+  q.mask = P->mask;
+  q.maxslot = scratch + 2;
+  q.n_frames = nf;
+  q.warps_per_block = P->post_wpb;
+  post_spec(q, &c->sq);
+  LogParams& l = c->l;
+  l.out = out;
+  l.planes = planes;
+  l.n_out = P->n_out;
+  l.s_src = s_env;
+  l.s_dst = stage_index(stages, PA_STAGE_LOG);
+  l.plane_elems = (long long)d.nx * d.nz;
+  l.maxslot = scratch + 2;
+  l.dyn_range_db = P->dyn_range;
+  l.n_frames = nf;
+  log_spec(l, P->num_sms, &c->sl);
+}
+
+pa_status launch_direct(pa_plan_s* P, ChunkLaunch& c, cudaStream_t st) {
+  k_zero_ints<<<1, 256, 0, st>>>(c.zero, (int)c.zero_ints);
+  PA_CUDA(cudaGetLastError());
   {
     ProfScope ps(P, 0, st);
-    PA_CUDA(bf_launch(P->K, P->apod, P->comp, b, grid, P->threads, P->smem, st));
+    void* args[] = {&c.b};
+    PA_CUDA(cudaLaunchKernel(c.sb.func, c.sb.grid, c.sb.block, args, c.sb.smem, st));
   }
-
-  if (stages & (PA_STAGE_ENV | PA_STAGE_LOG)) {
-    PostParams q;
-    q.out = out;
-    q.planes = planes;
-    q.n_out = P->n_out;
-    q.s_src = s_raw;
-    q.s_dst = s_env;
-    q.nx = d.nx;
-    q.nz = d.nz;
-    q.m = P->M;
-    q.log2m = P->log2M;
-    q.tw = P->tw;
-    q.mask = P->mask;
-    q.maxslot = scratch + 2;
-    q.n_frames = nf;
-    q.warps_per_block = P->post_wpb;
+  if (c.post) {
     ProfScope ps(P, 1, st);
-    PA_CUDA(post_launch(q, st));
+    void* args[] = {&c.q};
+    PA_CUDA(cudaLaunchKernel(c.sq.func, c.sq.grid, c.sq.block, args, c.sq.smem, st));
   }
-  if (stages & PA_STAGE_LOG) {
-    LogParams l;
-    l.out = out;
-    l.planes = planes;
-    l.n_out = P->n_out;
-    l.s_src = s_env;
-    l.s_dst = stage_index(stages, PA_STAGE_LOG);
-    l.plane_elems = (long long)d.nx * d.nz;
-    l.maxslot = scratch + 2;
-    l.dyn_range_db = P->dyn_range;
-    l.n_frames = nf;
+  if (c.log) {
     ProfScope ps(P, 2, st);
-    PA_CUDA(log_launch(l, P->num_sms, st));
+    void* args[] = {&c.l};
+    PA_CUDA(cudaLaunchKernel(c.sl.func, c.sl.grid, c.sl.block, args, c.sl.smem, st));
   }
   return PA_OK;
+}
+
+cudaKernelNodeParams node_params(const LaunchSpec& s, void** args) {
+  cudaKernelNodeParams k{};
+  k.func = const_cast<void*>(s.func);
+  k.gridDim = s.grid;
+  k.blockDim = s.block;
+  k.sharedMemBytes = (unsigned)s.smem;
+  k.kernelParams = args;
+  k.extra = nullptr;
+  return k;
+}
+
+
+// One chunk as a CUDA graph: clear -> fused kernel [-> post [-> log]].  An
+// executable graph is kept per (frames, stages); later calls only rewrite the
+// node parameters (buffer pointers) and launch it.
+pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cudaStream_t st) {
+  pa_plan_s::GraphEntry* ge = nullptr;
+  for (auto& g : P->graphs)
+    if (g.nf == nf && g.stages == stages) ge = &g;
+  void* ab[] = {&c.b};
+  void* aq[] = {&c.q};
+  void* al[] = {&c.l};
+  int zn = (int)c.zero_ints;
+  void* az[] = {&c.zero, &zn};
+  LaunchSpec sz;
+  sz.func = reinterpret_cast<const void*>(k_zero_ints);
+  sz.grid = dim3(1);
+  sz.block = dim3(256);
+  const cudaKernelNodeParams kz = node_params(sz, az);
+  const cudaKernelNodeParams kb = node_params(c.sb, ab);
+  const cudaKernelNodeParams kq = node_params(c.sq, aq);
+  const cudaKernelNodeParams kl = node_params(c.sl, al);
+  if (!ge) {
+    pa_plan_s::GraphEntry g;
+    g.nf = nf;
+    g.stages = stages;
+    cudaGraph_t graph;
+    PA_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphNode_t prev;
+    cudaError_t e = cudaGraphAddKernelNode(&g.n_memset, graph, nullptr, 0, &kz);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g.n_bf, graph, &g.n_memset, 1, &kb);
+    prev = g.n_bf;
+    if (e == cudaSuccess && c.post) {
+      e = cudaGraphAddKernelNode(&g.n_post, graph, &prev, 1, &kq);
+      prev = g.n_post;
+    }
+    if (e == cudaSuccess && c.log) e = cudaGraphAddKernelNode(&g.n_log, graph, &prev, 1, &kl);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return fail(PA_ECUDA, "graph build: %s", cudaGetErrorString(e));
+    }
+    g.graph = graph;
+    P->graphs.push_back(g);
+    ge = &P->graphs.back();
+  } else {
+    PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_memset, &kz));
+    PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_bf, &kb));
+    if (c.post) PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_post, &kq));
+    if (c.log) PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_log, &kl));
+  }
+  PA_CUDA(cudaGraphLaunch(ge->exec, st));
+  return PA_OK;
+}
+
+// One launch sequence for nf <= max_batch frames.  Kernel timing needs the
+// direct launches (events bracket each kernel); otherwise the plan's graphs
+// are used when enabled.
+pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                    cudaStream_t st, int* scratch) {
+  ChunkLaunch c;
+  prepare_chunk(P, rf, nf, out, stages, scratch, &c);
+  if (P->use_graph && !P->prof) return launch_graph(P, c, nf, stages, st);
+  return launch_direct(P, c, st);
 }
 
 }  // namespace
@@ -694,6 +815,19 @@ cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p, int gr
     case 8: return bf_launch_k8(apod, comp, p, grid, block, smem, s);
   }
   return cudaErrorInvalidValue;
+}
+const void* bf_func(int order, bool apod, bool comp) {
+  switch (order) {
+    case 1: return bf_func_k1(apod, comp);
+    case 2: return bf_func_k2(apod, comp);
+    case 3: return bf_func_k3(apod, comp);
+    case 4: return bf_func_k4(apod, comp);
+    case 5: return bf_func_k5(apod, comp);
+    case 6: return bf_func_k6(apod, comp);
+    case 7: return bf_func_k7(apod, comp);
+    case 8: return bf_func_k8(apod, comp);
+  }
+  return nullptr;
 }
 cudaError_t bf_occupancy(int order, bool apod, bool comp, int block, size_t smem, int* n) {
   switch (order) {
@@ -865,6 +999,12 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   }
   PA_CUDA(cudaStreamSynchronize(P->hs[0]));
   PA_CUDA(cudaStreamSynchronize(P->hs[1]));
+  return PA_OK;
+}
+
+pa_status pa_plan_use_graph(pa_plan_t P, int32_t enable) {
+  if (!P) return fail(PA_EINVAL, "null plan");
+  P->use_graph = enable != 0;
   return PA_OK;
 }
 

@@ -288,24 +288,39 @@ cudaError_t post_configure(size_t smem) {
   return cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t post_launch(const PostParams& p, cudaStream_t s) {
+void post_spec(const PostParams& p, LaunchSpec* ls) {
   const size_t mp = (size_t)p.m + (p.m >> 3);
-  const size_t smem = ((size_t)p.warps_per_block * 3 * mp + p.m) * sizeof(float2);
+  ls->func = reinterpret_cast<const void*>(k_post);
+  ls->smem = ((size_t)p.warps_per_block * 3 * mp + p.m) * sizeof(float2);
   const int col_pairs = (p.nx + 1) / 2;
-  dim3 grid((col_pairs + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
-  k_post<<<grid, p.warps_per_block * 32, smem, s>>>(p);
-  return cudaGetLastError();
+  ls->grid = dim3((col_pairs + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
+  ls->block = dim3(p.warps_per_block * 32);
 }
 
-cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s) {
+void log_spec(const LogParams& p, int num_sms, LaunchSpec* ls) {
   long long blocks = (p.plane_elems / 4 + 255) / 256 + 1;
   const long long images = (long long)p.n_frames * p.n_out;
   const long long target = (long long)num_sms * 32;
   long long per_img = (target + images - 1) / images;
   if (per_img < 1) per_img = 1;
   if (blocks > per_img) blocks = per_img;
-  dim3 grid((unsigned)blocks, (unsigned)images);
-  k_log<<<grid, 256, 0, s>>>(p);
+  ls->func = reinterpret_cast<const void*>(k_log);
+  ls->grid = dim3((unsigned)blocks, (unsigned)images);
+  ls->block = dim3(256);
+  ls->smem = 0;
+}
+
+cudaError_t post_launch(const PostParams& p, cudaStream_t s) {
+  LaunchSpec ls;
+  post_spec(p, &ls);
+  k_post<<<ls.grid, ls.block, ls.smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s) {
+  LaunchSpec ls;
+  log_spec(p, num_sms, &ls);
+  k_log<<<ls.grid, ls.block, ls.smem, s>>>(p);
   return cudaGetLastError();
 }
 

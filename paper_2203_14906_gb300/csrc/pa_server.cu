@@ -1,0 +1,476 @@
+// pa_server.cu -- continuous-batching request server over the plan ABI.
+//
+// One scheduler thread owns every CUDA call of the server: plan creation,
+// device buffers (a stream-ordered memory pool), the H2D copy, pa_beamform
+// and the D2H copy of each batch, and completion polling.  Callers only
+// enqueue requests and wait for results, so the plan objects (which are not
+// thread-safe) are touched by one thread.
+//
+// Scheduling: requests become visible at their arrival time.  Whenever a
+// slot (stream) is free, the oldest visible request whose plan is not busy
+// in another slot is taken, with up to max_batch - 1 later visible requests
+// of the same descriptor; the batch is admitted if its buffers (and a new
+// plan's tables) fit in the device budget next to the batches in flight.
+// Completion is detected by polling each slot's event; the request's latency
+// is the server-clock time of that detection minus its arrival time.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pa_internal.cuh"
+
+namespace {
+
+using clock_type = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  pa_plan_desc desc{};
+  std::string key;
+  const void* rf = nullptr;
+  float* out = nullptr;
+  size_t rf_bytes = 0, out_bytes = 0;
+  double arrival = 0, start = 0, done = 0;
+  pa_status status = PA_OK;
+  int batch = 0;
+  bool finished = false;
+};
+
+struct PlanEntry {
+  pa_plan_t plan = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  uint64_t last_used = 0;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  std::vector<Request*> reqs;
+  size_t bytes = 0;
+  PlanEntry* pe = nullptr;
+};
+
+std::string plan_key(const pa_plan_desc& d) {
+  char buf[640];
+  snprintf(buf, sizeof buf,
+           "%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%u|%d|%.17g|%.17g|%.17g|"
+           "%.17g|%.17g|%d",
+           d.n_elem, d.pitch_m, d.c_m_s, d.fs_hz, d.t0_s, d.n_samples, d.nx, d.nz, d.x0_m, d.x1_m,
+           d.z0_m, d.z1_m, d.order_k, d.outputs, (int)d.rf_dtype, d.f_number, d.f0_hz,
+           d.band_lo_hz, d.band_hi_hz, d.dyn_range_db, d.compensated);
+  return buf;
+}
+
+int popc3(uint32_t m) { return (int)((m & 1u) + ((m >> 1) & 1u) + ((m >> 2) & 1u)); }
+
+size_t align_up(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct pa_server_s {
+  pa_server_config cfg{};
+  int device = 0;
+  clock_type::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_done;
+  std::multimap<double, Request*> pending;  // submitted, by arrival time
+  std::unordered_map<uint64_t, Request*> by_ticket;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  // scheduler-thread state
+  std::list<Request*> visible;  // arrived, not yet issued, in arrival order
+  std::map<std::string, PlanEntry> plans;
+  std::vector<Slot> slots;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t plan_stream = nullptr;
+  uint64_t use_clock = 0;
+  // statistics (guarded by mu)
+  uint64_t submitted = 0, completed = 0, failed = 0, batches = 0;
+  size_t in_use = 0, peak = 0;
+  std::thread th;
+
+  double now() const {
+    return std::chrono::duration<double>(clock_type::now() - t0).count();
+  }
+
+  void finish(Request* r, pa_status st, double t) {
+    // caller holds mu
+    r->status = st;
+    r->done = t;
+    r->finished = true;
+    if (st == PA_OK) ++completed;
+    else ++failed;
+  }
+
+  // Poll slots; returns true if any batch completed.
+  bool reap() {
+    bool any = false;
+    for (auto& s : slots) {
+      if (!s.busy) continue;
+      cudaError_t e = cudaEventQuery(s.ev);
+      if (e == cudaErrorNotReady) continue;
+      const double t = now();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (Request* r : s.reqs) finish(r, e == cudaSuccess ? PA_OK : PA_ECUDA, t);
+        in_use -= s.bytes;
+      }
+      if (e != cudaSuccess) cudaGetLastError();
+      s.pe->busy = false;
+      s.busy = false;
+      s.reqs.clear();
+      s.bytes = 0;
+      any = true;
+    }
+    if (any) cv_done.notify_all();
+    return any;
+  }
+
+  // Destroy least recently used idle plans until `need` more bytes fit.
+  void evict_for(size_t need) {
+    for (;;) {
+      size_t cur;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        cur = in_use;
+      }
+      const bool over_count = (int)plans.size() > std::max(1, cfg.max_plans);
+      if (cur + need <= cfg.device_budget_bytes && !over_count) return;
+      auto victim = plans.end();
+      for (auto it = plans.begin(); it != plans.end(); ++it) {
+        if (it->second.busy) continue;
+        if (victim == plans.end() || it->second.last_used < victim->second.last_used) victim = it;
+      }
+      if (victim == plans.end()) return;
+      pa_destroy(victim->second.plan);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= victim->second.bytes;
+      }
+      plans.erase(victim);
+    }
+  }
+
+  // Try to issue one batch on slot s; returns true if something was issued
+  // or failed (the visible list changed).
+  bool issue(Slot& s) {
+    for (auto it = visible.begin(); it != visible.end(); ++it) {
+      Request* head = *it;
+      auto pit = plans.find(head->key);
+      if (pit != plans.end() && pit->second.busy) continue;  // plan in flight elsewhere
+      std::vector<std::list<Request*>::iterator> pick{it};
+      for (auto jt = std::next(it); jt != visible.end() && (int)pick.size() < cfg.max_batch; ++jt)
+        if ((*jt)->key == head->key) pick.push_back(jt);
+      const int nf = (int)pick.size();
+      const size_t buf_rf = align_up(head->rf_bytes * nf), buf_out = align_up(head->out_bytes * nf);
+      size_t plan_bytes = 0;
+      if (pit == plans.end()) {
+        pa_plan_desc d = head->desc;
+        d.max_batch = cfg.max_batch;
+        if (pa_plan_footprint(&d, 0, &plan_bytes) != PA_OK) plan_bytes = 0;
+      }
+      const size_t need = buf_rf + buf_out + plan_bytes;
+      evict_for(need);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        if (in_use + need > cfg.device_budget_bytes) return false;  // wait for memory
+      }
+      if (pit == plans.end()) {
+        pa_plan_desc d = head->desc;
+        d.max_batch = cfg.max_batch;
+        PlanEntry pe;
+        const pa_status st = pa_plan(&d, plan_stream, &pe.plan);
+        if (st != PA_OK) {
+          std::lock_guard<std::mutex> lk(mu);
+          finish(head, st, now());
+          visible.erase(it);
+          cv_done.notify_all();
+          return true;
+        }
+        pa_plan_info inf;
+        pa_plan_get_info(pe.plan, &inf);
+        pe.bytes = inf.device_bytes;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          in_use += pe.bytes;
+          peak = std::max(peak, in_use);
+        }
+        pit = plans.emplace(head->key, pe).first;
+      }
+      PlanEntry& pe = pit->second;
+      void* rf_dev = nullptr;
+      void* out_dev = nullptr;
+      cudaError_t e = cudaMallocFromPoolAsync(&rf_dev, buf_rf, pool, s.st);
+      if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&out_dev, buf_out, pool, s.st);
+      pa_status st = PA_OK;
+      if (e == cudaSuccess) {
+        for (int q = 0; q < nf && e == cudaSuccess; ++q) {
+          Request* r = *pick[q];
+          e = cudaMemcpyAsync((char*)rf_dev + q * r->rf_bytes, r->rf, r->rf_bytes,
+                              cudaMemcpyHostToDevice, s.st);
+        }
+      }
+      if (e == cudaSuccess) {
+        st = pa_beamform(pe.plan, rf_dev, nf, (float*)out_dev, cfg.stages, s.st);
+        for (int q = 0; q < nf && st == PA_OK && e == cudaSuccess; ++q) {
+          Request* r = *pick[q];
+          e = cudaMemcpyAsync(r->out, (char*)out_dev + q * r->out_bytes, r->out_bytes,
+                              cudaMemcpyDeviceToHost, s.st);
+        }
+      }
+      if (rf_dev) cudaFreeAsync(rf_dev, s.st);
+      if (out_dev) cudaFreeAsync(out_dev, s.st);
+      if (e == cudaSuccess && st == PA_OK) e = cudaEventRecord(s.ev, s.st);
+      const double t = now();
+      std::lock_guard<std::mutex> lk(mu);
+      if (e != cudaSuccess || st != PA_OK) {
+        cudaGetLastError();
+        for (auto& p : pick) finish(*p, st != PA_OK ? st : PA_ECUDA, t);
+        for (auto& p : pick) visible.erase(p);
+        cv_done.notify_all();
+        return true;
+      }
+      s.busy = true;
+      s.pe = &pe;
+      s.bytes = buf_rf + buf_out;
+      in_use += s.bytes;
+      peak = std::max(peak, in_use);
+      pe.busy = true;
+      pe.last_used = ++use_clock;
+      ++batches;
+      for (auto& p : pick) {
+        (*p)->start = t;
+        (*p)->batch = nf;
+        s.reqs.push_back(*p);
+      }
+      for (auto& p : pick) visible.erase(p);
+      return true;
+    }
+    return false;
+  }
+
+  void loop() {
+    cudaSetDevice(device);
+    for (;;) {
+      double next_arrival = -1;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        const double t = now();
+        while (!pending.empty() && pending.begin()->first <= t) {
+          visible.push_back(pending.begin()->second);
+          pending.erase(pending.begin());
+        }
+        if (!pending.empty()) next_arrival = pending.begin()->first;
+        bool busy = false;
+        for (auto& s : slots) busy = busy || s.busy;
+        if (stop && !busy) break;
+        if (!busy && visible.empty()) {
+          // nothing to run or poll: sleep until the next arrival or a submit
+          if (next_arrival < 0) cv_sched.wait_for(lk, std::chrono::milliseconds(50));
+          else cv_sched.wait_for(lk, std::chrono::duration<double>(std::max(0.0, next_arrival - t)));
+          continue;
+        }
+      }
+      bool progress = reap();
+      if (!stop) {
+        for (auto& s : slots) {
+          if (s.busy || visible.empty()) continue;
+          progress = issue(s) || progress;
+        }
+      }
+      if (!progress) {
+        // slots busy or waiting for memory: poll again shortly (bounded wait)
+        std::unique_lock<std::mutex> lk(mu);
+        double wait_s = 20e-6;
+        if (next_arrival >= 0) wait_s = std::min(wait_s, std::max(0.0, next_arrival - now()));
+        cv_sched.wait_for(lk, std::chrono::duration<double>(wait_s));
+      }
+    }
+  }
+};
+
+extern "C" {
+
+pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
+  if (!cfg || !out) {
+    pa::set_error_message("pa_server_create: null argument");
+    return PA_EINVAL;
+  }
+  *out = nullptr;
+  if (cfg->slots < 1 || cfg->max_batch < 1 || cfg->device_budget_bytes == 0 ||
+      (cfg->stages & 7u) == 0 || (cfg->stages & ~7u)) {
+    pa::set_error_message("pa_server_create: slots, max_batch, budget and stages must be set");
+    return PA_EINVAL;
+  }
+  pa_server_s* S = new pa_server_s();
+  S->cfg = *cfg;
+  if (S->cfg.max_plans < 1) S->cfg.max_plans = 1 << 20;
+  cudaError_t e = cudaGetDevice(&S->device);
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = S->device;
+  if (e == cudaSuccess) e = cudaMemPoolCreate(&S->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
+    e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->plan_stream, cudaStreamNonBlocking);
+  S->slots.resize(cfg->slots);
+  for (auto& s : S->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    pa::set_error_message(cudaGetErrorString(e));
+    for (auto& s : S->slots) {
+      if (s.st) cudaStreamDestroy(s.st);
+      if (s.ev) cudaEventDestroy(s.ev);
+    }
+    if (S->plan_stream) cudaStreamDestroy(S->plan_stream);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    delete S;
+    return PA_ECUDA;
+  }
+  S->t0 = clock_type::now();
+  S->th = std::thread([S] { S->loop(); });
+  *out = S;
+  return PA_OK;
+}
+
+double pa_server_now(pa_server_t S) { return S ? S->now() : 0.0; }
+
+pa_status pa_server_submit(pa_server_t S, const pa_plan_desc* desc, const void* rf_host,
+                           float* out_host, double arrival_s, uint64_t* ticket) {
+  if (!S || !desc || !rf_host || !out_host || !ticket) {
+    pa::set_error_message("pa_server_submit: null argument");
+    return PA_EINVAL;
+  }
+  pa_plan_desc d = *desc;
+  d.max_batch = S->cfg.max_batch;
+  size_t one = 0;
+  pa_status st = pa_plan_footprint(&d, 1, &one);
+  if (st != PA_OK) return st;  // message already set
+  Request* r = new Request();
+  r->desc = d;
+  r->key = plan_key(d);
+  r->rf = rf_host;
+  r->out = out_host;
+  r->rf_bytes = (size_t)d.n_elem * d.n_samples * (d.rf_dtype == PA_RF_F32 ? 4 : 2);
+  r->out_bytes = (size_t)popc3(S->cfg.stages) * popc3(d.outputs) * d.nx * d.nz * sizeof(float);
+  size_t plan_bytes = 0;
+  pa_plan_footprint(&d, 0, &plan_bytes);
+  if (plan_bytes + align_up(r->rf_bytes) + align_up(r->out_bytes) > S->cfg.device_budget_bytes) {
+    delete r;
+    pa::set_error_message("pa_server_submit: one frame needs more device memory than the budget");
+    return PA_ENOMEM;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      delete r;
+      pa::set_error_message("pa_server_submit: server is stopping");
+      return PA_EBUSY;
+    }
+    r->ticket = S->next_ticket++;
+    r->arrival = arrival_s > 0 ? arrival_s : S->now();
+    S->pending.emplace(r->arrival, r);
+    S->by_ticket[r->ticket] = r;
+    ++S->submitted;
+    *ticket = r->ticket;
+  }
+  S->cv_sched.notify_one();
+  return PA_OK;
+}
+
+pa_status pa_server_wait(pa_server_t S, uint64_t ticket, int32_t timeout_ms,
+                         pa_request_result* res) {
+  if (!S || !res) {
+    pa::set_error_message("pa_server_wait: null argument");
+    return PA_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->by_ticket.find(ticket);
+  if (it == S->by_ticket.end()) {
+    pa::set_error_message("pa_server_wait: unknown ticket (or result already read)");
+    return PA_EINVAL;
+  }
+  Request* r = it->second;
+  auto ready = [&] { return r->finished; };
+  if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+    pa::set_error_message("pa_server_wait: request still pending");
+    return PA_ETIMEOUT;
+  }
+  res->ticket = r->ticket;
+  res->status = r->status;
+  res->arrival_s = r->arrival;
+  res->start_s = r->start;
+  res->done_s = r->done;
+  res->latency_ms = (r->done - r->arrival) * 1e3;
+  res->batch_frames = r->batch;
+  S->by_ticket.erase(it);
+  delete r;
+  return PA_OK;
+}
+
+pa_status pa_server_get_stats(pa_server_t S, pa_server_stats* st) {
+  if (!S || !st) {
+    pa::set_error_message("pa_server_get_stats: null argument");
+    return PA_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  st->submitted = S->submitted;
+  st->completed = S->completed;
+  st->failed = S->failed;
+  st->batches = S->batches;
+  st->bytes_in_use = S->in_use;
+  st->bytes_peak = S->peak;
+  st->plans_resident = (int32_t)S->plans.size();
+  return PA_OK;
+}
+
+pa_status pa_server_destroy(pa_server_t S) {
+  if (!S) return PA_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_sched.notify_all();
+  if (S->th.joinable()) S->th.join();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    const double t = S->now();
+    for (auto& p : S->pending) S->finish(p.second, PA_EBUSY, t);
+    for (Request* r : S->visible) S->finish(r, PA_EBUSY, t);
+    S->pending.clear();
+    S->visible.clear();
+    for (auto& kv : S->by_ticket) delete kv.second;
+    S->by_ticket.clear();
+  }
+  S->cv_done.notify_all();
+  for (auto& kv : S->plans) pa_destroy(kv.second.plan);
+  for (auto& s : S->slots) {
+    cudaStreamSynchronize(s.st);
+    cudaStreamDestroy(s.st);
+    cudaEventDestroy(s.ev);
+  }
+  cudaStreamDestroy(S->plan_stream);
+  cudaMemPoolDestroy(S->pool);
+  delete S;
+  return PA_OK;
+}
+
+}  // extern "C"

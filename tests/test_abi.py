@@ -122,3 +122,21 @@ def test_oracle_and_cuda_sources_share_nothing():
 def test_build_is_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
     assert os.path.exists(_build.build())
+
+
+def test_server_config_validation_without_gpu():
+    from paper_2203_14906_gb300 import serving
+
+    L = _native.load()
+    serving._bind(L)
+    h = ctypes.c_void_p()
+    bad = serving.ServerConfig(0, 1, 1, 1, 4)  # zero budget
+    assert L.pa_server_create(ctypes.byref(bad), ctypes.byref(h)) == _native.PA_EINVAL
+    bad = serving.ServerConfig(1 << 30, 0, 1, 1, 4)  # no slots
+    assert L.pa_server_create(ctypes.byref(bad), ctypes.byref(h)) == _native.PA_EINVAL
+    bad = serving.ServerConfig(1 << 30, 1, 1, 1, 8)  # bad stage mask
+    assert L.pa_server_create(ctypes.byref(bad), ctypes.byref(h)) == _native.PA_EINVAL
+    t = ctypes.c_uint64()
+    d = _native.make_desc(synth.workload("cfg1"))
+    assert L.pa_server_submit(None, ctypes.byref(d), None, None, 0.0, ctypes.byref(t)) == _native.PA_EINVAL
+    assert L.pa_server_destroy(None) == _native.PA_OK

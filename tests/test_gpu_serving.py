@@ -1,0 +1,132 @@
+"""Continuous-batching server (pa_server_*) on the GPU.
+
+* A request's images are bitwise identical alone, in a mixed burst of other
+  geometries / orders, and through a direct pa_beamform call.
+* Same-descriptor requests that arrive together are batched; batches of
+  different requests overlap on the device (several slots in flight).
+* Admission by device memory: a budget that fits one batch at a time still
+  completes every request and never exceeds the budget.
+* Host-side failure paths: a request whose arrival never comes times out, a
+  malformed descriptor and a frame larger than the budget are rejected at
+  submit time.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+LOG = 4
+
+
+def _frame(wl, seed, dtype="bf16"):
+    import torch
+
+    store, _ = synth.quantize(synth.make_frame(wl, seed), dtype)
+    if dtype == "bf16":
+        return torch.from_numpy(store.view(np.int16)).pin_memory()
+    return torch.from_numpy(store).pin_memory()
+
+
+def _mix_workloads():
+    a = synth.workload("cfg1", rf_dtype="bf16", compensated=1)
+    b = synth.workload("cfg1", rf_dtype="bf16", compensated=1, n_elem=32, nx=128, nz=96, z1_m=12e-3)
+    b["x0_m"], b["x1_m"] = -32 * 0.15e-3, 32 * 0.15e-3
+    c = synth.workload("cfg1", rf_dtype="bf16", compensated=1, nx=256, nz=128, n_samples=2048)
+    return [(a, 3), (b, 5), (c, 2), (a, 4)]
+
+
+def _out(pa, wl, k, stages=LOG):
+    import torch
+
+    d = pa.make_desc(wl, order_k=k)
+    n_out = bin(d.outputs).count("1")
+    return torch.zeros((bin(stages).count("1"), n_out, wl["nx"], wl["nz"]),
+                       dtype=torch.float32).pin_memory()
+
+
+def test_alone_equals_mix_equals_direct():
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300.serving import Server
+
+    wl, k = _mix_workloads()[0]
+    rf = _frame(wl, 1)
+    # direct call
+    with pa.Plan(pa.make_desc(wl, order_k=k)) as plan:
+        direct = pa.beamform(plan, rf.cuda()[None].view(torch.bfloat16), LOG).cpu()[0]
+    with Server(budget_bytes=2 << 30, slots=4, max_batch=4) as srv:
+        alone = _out(pa, wl, k)
+        t = srv.submit(pa.make_desc(wl, order_k=k), rf.data_ptr(), alone.data_ptr())
+        assert srv.wait(t)["status"] == 0
+        # the same frame inside a burst of other geometries and orders, all
+        # arriving at the same instant (so same-descriptor requests batch)
+        keep = []
+        tickets = []
+        t_burst = srv.now() + 0.2
+        for rep in range(3):
+            for i, (w, kk) in enumerate(_mix_workloads()):
+                f = _frame(w, 10 + i)
+                o = _out(pa, w, kk)
+                keep.append((f, o))
+                tickets.append(srv.submit(pa.make_desc(w, order_k=kk), f.data_ptr(), o.data_ptr(),
+                                          arrival_s=t_burst))
+        mixed = _out(pa, wl, k)
+        tm = srv.submit(pa.make_desc(wl, order_k=k), rf.data_ptr(), mixed.data_ptr(),
+                        arrival_s=t_burst)
+        res = [srv.wait(x) for x in tickets] + [srv.wait(tm)]
+        assert all(r["status"] == 0 for r in res)
+        st = srv.stats()
+    assert torch.equal(alone, direct)
+    assert torch.equal(mixed, direct)
+    assert st["completed"] == st["submitted"] == len(tickets) + 2
+    assert any(r["batch_frames"] > 1 for r in res)  # same-descriptor arrivals were batched
+    # at least two batches were in flight at the same time
+    iv = sorted((r["start_s"], r["done_s"]) for r in res)
+    assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1))
+
+
+def test_admission_under_tight_budget():
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300.serving import Server
+
+    wl, k = _mix_workloads()[2]
+    desc = pa.make_desc(wl, order_k=k)
+    one = pa.footprint(pa.make_desc(wl, order_k=k, max_batch=2), 2)
+    budget = int(one * 1.05)
+    frames = [(_frame(wl, s), _out(pa, wl, k)) for s in range(8)]
+    with Server(budget_bytes=budget, slots=4, max_batch=2) as srv:
+        ts = [srv.submit(desc, f.data_ptr(), o.data_ptr()) for f, o in frames]
+        res = [srv.wait(t, timeout_ms=60000) for t in ts]
+        st = srv.stats()
+    assert all(r["status"] == 0 for r in res)
+    assert st["bytes_peak"] <= budget
+    for f, o in frames:
+        assert float(o.abs().sum()) > 0
+
+
+def test_timeout_and_rejections():
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300._native import PA_EINVAL, PA_ENOMEM, PA_ETIMEOUT, PAError
+    from paper_2203_14906_gb300.serving import Server
+
+    wl, k = _mix_workloads()[0]
+    rf = _frame(wl, 3)
+    out = _out(pa, wl, k)
+    with Server(budget_bytes=1 << 30, slots=2, max_batch=2) as srv:
+        # arrival an hour from now: the producer "never posts"
+        t = srv.submit(pa.make_desc(wl, order_k=k), rf.data_ptr(), out.data_ptr(),
+                       arrival_s=srv.now() + 3600.0)
+        st, _ = srv.try_wait(t, 50)
+        assert st == PA_ETIMEOUT
+        bad = pa.make_desc(wl, order_k=9)
+        with pytest.raises(PAError) as e:
+            srv.submit(bad, rf.data_ptr(), out.data_ptr())
+        assert e.value.status == PA_EINVAL
+    with Server(budget_bytes=4096, slots=1, max_batch=1) as small:
+        with pytest.raises(PAError) as e:
+            small.submit(pa.make_desc(wl, order_k=k), rf.data_ptr(), out.data_ptr())
+        assert e.value.status == PA_ENOMEM
