@@ -106,10 +106,14 @@ typedef struct {
   int64_t active_pairs;       /* pairs with non-zero apodisation weight    */
   int64_t executed_pairs;     /* pairs the kernel evaluates per frame      */
   size_t device_bytes;        /* device memory owned by the plan now       */
+  int32_t tma_staging;        /* 1: RF windows staged by TMA boxes,
+                                 0: by vectorised loads                   */
   uint32_t device_error_flags; /* bounds-check flags raised by device code
-                                  since the plan was built (0 = none; only
-                                  checked builds raise them).  Reading it
-                                  synchronises the device.                 */
+                                  since the plan was built (0 = none): 1, 2
+                                  index checks (checked builds only), 8 a
+                                  TMA wait that ran out (the kernel stopped
+                                  early).  Reading it synchronises the
+                                  device.                                  */
 } pa_plan_info;
 
 /*

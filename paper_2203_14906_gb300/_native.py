@@ -83,6 +83,7 @@ class PlanInfo(ctypes.Structure):
         ("active_pairs", ctypes.c_int64),
         ("executed_pairs", ctypes.c_int64),
         ("device_bytes", ctypes.c_size_t),
+        ("tma_staging", ctypes.c_int32),
         ("device_error_flags", ctypes.c_uint32),
     ]
 
@@ -102,7 +103,11 @@ def load(checked: bool = False, build: bool = True):
     with _lock:
         if key in _libs:
             return _libs[key]
-        path = _build.build(checked=checked) if build else _build.lib_path(checked)
+        override = os.environ.get("PA_LIB_PATH")  # a library built elsewhere (comparisons)
+        if override:
+            path = override
+        else:
+            path = _build.build(checked=checked) if build else _build.lib_path(checked)
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA beamformer library missing: {path}")
         L = ctypes.CDLL(path)

@@ -191,7 +191,7 @@ __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int ti
   if (threadIdx.x < kNCS) {
     const int v = v0 + threadIdx.x;
     const int lo = v < p.nv ? __ldg(lo_t + v) : 0;
-    s_cb[threadIdx.x] = (int)sbase + kPairsOff + (int)threadIdx.x * W * 8 - lo * 8;
+    s_cb[threadIdx.x] = (int)sbase + p.pairs_off + (int)threadIdx.x * W * 8 - lo * 8;
   }
   const int total = kNCS * W4;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -215,10 +215,134 @@ __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int ti
         }
       }
     }
-    float4* dst = reinterpret_cast<float4*>(smem + kPairsOff + (size_t)(cv * W + 4 * q) * 8);
+    float4* dst = reinterpret_cast<float4*>(smem + p.pairs_off + (size_t)(cv * W + 4 * q) * 8);
     dst[0] = make_float4(r[0], r[1] - r[0], r[1], r[2] - r[1]);
     dst[1] = make_float4(r[2], r[3] - r[2], r[3], r[4] - r[3]);
   }
+}
+
+// ---- TMA staging ----------------------------------------------------------
+// One 1-D box of wr samples per staged channel, loaded by the tensor memory
+// accelerator straight from the 3-D RF map into the raw buffer; coordinates
+// outside the record (negative or >= Ns samples, channels outside [0, N))
+// read as zeros.  One mbarrier counts the bytes of a chunk.
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, int parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for the chunk with a bound of about one second of SM clock; returns
+// false if the bytes never arrived.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, int parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(mbar, parity)) {
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                        uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+// The boxes of a chunk are issued by kNCS threads spread over the warps
+// (staged channel cv = lane * nwarps + warp; blocks have at least two warps,
+// so ceil(kNCS / nwarps) <= 18 lanes per warp suffice), so no warp falls
+// behind the others; each issuing thread keeps its channel's next window
+// start in a register, loaded one chunk ahead.
+__device__ __forceinline__ int tma_channel() {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int cv = lane * nwarps + warp;
+  return (lane * nwarps < kNCS && cv < kNCS) ? cv : -1;
+}
+
+__device__ __forceinline__ int window_start(const BfParams& p, int tile_id, int k, int cv) {
+  const int v = k * kNC + cv;
+  return v < p.nv ? __ldg(p.lo + (size_t)tile_id * p.nv + v) : 0;
+}
+
+// Issue the boxes of chunk k of (tile, frame); every thread calls it.
+__device__ __forceinline__ void tma_issue_chunk(const BfParams& p, int frame, int k, int cv, int lo,
+                                                int* s_lo, uint32_t raw_s, uint32_t mbar) {
+  if (threadIdx.x == 0) mbar_expect(mbar, p.chunk_bytes);
+  if (cv >= 0) {
+    const int elt = p.rf_dtype == PA_RF_F32 ? 4 : 2;
+    s_lo[cv] = lo;
+    tma_box(raw_s + (uint32_t)(cv * p.rp * elt), &p.tmap, lo, k * kNC + cv + p.u0, frame, mbar);
+  }
+}
+
+// Raw samples of a chunk -> (r[n], r[n+1] - r[n]) slots and channel bases.
+template <int DT>
+__device__ __forceinline__ void convert_chunk(const BfParams& p, int* s_cb, const int* s_lo,
+                                              unsigned char* smem, uint32_t sbase) {
+  const int W = p.window, W4 = W >> 2;
+  if (threadIdx.x < kNCS)
+    s_cb[threadIdx.x] = (int)sbase + p.pairs_off + (int)threadIdx.x * W * 8 - s_lo[threadIdx.x] * 8;
+  const int total = kNCS * W4;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
+    const int q = idx - cv * W4;
+    const int base = cv * p.rp + 4 * q;
+    float r[5];
+    if constexpr (DT == PA_RF_F32) {
+      const float* raw = reinterpret_cast<const float*>(smem + kRawOff);
+      const float4 v = *reinterpret_cast<const float4*>(raw + base);
+      r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+      r[4] = raw[base + 4];
+    } else {
+      const unsigned short* raw = reinterpret_cast<const unsigned short*>(smem + kRawOff);
+      const uint2 v = *reinterpret_cast<const uint2*>(raw + base);
+      const unsigned w[5] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16, raw[base + 4]};
+#pragma unroll
+      for (int t = 0; t < 5; ++t) {
+        if constexpr (DT == PA_RF_BF16) r[t] = __uint_as_float(w[t] << 16);
+        else r[t] = __half2float(__ushort_as_half((unsigned short)w[t]));
+      }
+    }
+    float4* dst = reinterpret_cast<float4*>(smem + p.pairs_off + (size_t)(cv * W + 4 * q) * 8);
+    dst[0] = make_float4(r[0], r[1] - r[0], r[1], r[2] - r[1]);
+    dst[1] = make_float4(r[2], r[3] - r[2], r[3], r[4] - r[3]);
+  }
+}
+
+struct ItemInfo {
+  int tile_id, grp, frame, tz, tx;
+};
+
+// Work item = (tile, residue group) x frame, frame fastest; the host-built
+// item table lists (tile, group) pairs deepest tiles first.
+__device__ __forceinline__ ItemInfo decode_item(const BfParams& p, int item) {
+  ItemInfo it;
+  const int tg = item / p.n_frames;
+  it.frame = item - tg * p.n_frames;
+  const int4 e = __ldg(p.items + tg);
+  it.tile_id = e.x;
+  it.grp = e.y;
+  it.tx = e.z;
+  it.tz = e.w;
+  return it;
 }
 
 template <int NA>
@@ -240,43 +364,55 @@ __device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC
 // Resident 256-thread blocks per SM the register allocation targets: three
 // (80 registers) for plain sums of orders <= 5, two for the larger accumulator
 // sets of compensated sums and orders >= 6.
+#ifndef PA_MINB4_MAX_K
+#define PA_MINB4_MAX_K 3
+#endif
 template <int K, bool COMP>
 struct MinBlocks {
-  static constexpr int value = (COMP || K >= 6) ? 2 : 3;
+  static constexpr int value = (COMP || K >= 6) ? 2 : (K <= PA_MINB4_MAX_K ? 4 : 3);
 };
 
 template <int K, bool APOD, bool COMP>
-__global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(const BfParams p) {
+__global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
+    k_bf_fused(const __grid_constant__ BfParams p) {
   constexpr int NA = NAcc<K>::value;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
+  // [0] item to run next, [1] its first chunk is already loading, [2] the
+  // item after it (taken from the counter one item ahead)
   int* s_item = reinterpret_cast<int*>(smem);
-  int* s_cb = reinterpret_cast<int*>(smem + 16);
+  int* s_cb = reinterpret_cast<int*>(smem + kCbOff);
+  int* s_lo = reinterpret_cast<int*>(smem + kLoOff);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-  const int pairs_off = (int)sbase + kPairsOff;
+  const uint32_t mbar = sbase + kMbarOff;
+  const int my_cv = tma_channel();
+  const uint32_t raw_s = sbase + kRawOff;
+  const int pairs_off = (int)sbase + p.pairs_off;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int per_tile = p.ngroups * p.n_frames;
-  const int mstride = p.m * p.table_stride;
 #ifdef PA_CHECK_BOUNDS
   const int smem_hi = pairs_off + kNCS * p.window * 8 - 8;  // shared addresses
 #endif
+  int phase = 0;
+  if (threadIdx.x == 0) {
+    if (p.use_tma) mbar_init(mbar);
+    s_item[0] = atomicAdd(p.counter, 1);
+    s_item[1] = 0;
+    s_item[2] = 0;
+  }
+  __syncthreads();
 
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item[0] = atomicAdd(p.counter, 1);
-    __syncthreads();
     const int item = s_item[0];
+    const bool prefetched = s_item[1] != 0;
+    __syncthreads();
     if (item >= p.n_items) break;
-    const int t = item / per_tile;
-    const int rem = item - t * per_tile;
-    const int grp = rem / p.n_frames;
-    const int frame = rem - grp * p.n_frames;
-    const int tz = p.nzt - 1 - t / p.nxt;  // deepest tiles first
-    const int tx = t % p.nxt;
-    const int tile_id = tz * p.nxt + tx;
+    if (threadIdx.x == 0) s_item[2] = atomicAdd(p.counter, 1);
+    const ItemInfo it = decode_item(p, item);
+    const int tz = it.tz, tx = it.tx, tile_id = it.tile_id, grp = it.grp, frame = it.frame;
     const int sl = grp * nwarps + warp;
-    const int r_m = sl % p.m, g = sl / p.m;
+    const int2 rg = __ldg(p.slot_rg + sl);
+    const int r_m = rg.x, g = rg.y;
     const int jt = tx * p.tile_x + g * p.m * kC + r_m;
     const int z = tz * p.tile_z + lane;
     const int2 ur = __ldg(p.urange + (size_t)tile_id * p.slots + sl);
@@ -297,16 +433,67 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(c
     }
     int fold = 0;
 
+    // Table rows of this thread: row t(u) = jt - dmin - m u at depth z.
     const int2* tcol = p.table + z;
     const float* wcol = APOD ? p.wtab + z : nullptr;
-    const int row_u0 = jt - p.dmin;  // table row at channel step u = 0
+    const int row_u0 = jt - p.dmin;
+    const int mstride = p.m * p.table_stride;
 
+    int lo_next = 0;  // window start of my channel in the next chunk to issue
+    if (p.use_tma && vk.x < vk.y) {
+      if (!prefetched) {
+        if (my_cv >= 0) lo_next = window_start(p, tile_id, vk.x, my_cv);
+        tma_issue_chunk(p, frame, vk.x, my_cv, lo_next, s_lo, raw_s, mbar);
+      }
+      if (my_cv >= 0 && vk.x + 1 < vk.y) lo_next = window_start(p, tile_id, vk.x + 1, my_cv);
+    }
+    bool timed_out = false;
     for (int k = vk.x; k < vk.y; ++k) {
-      __syncthreads();
-      if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
-      else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
-      else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
-      __syncthreads();
+      if (p.use_tma) {
+        // raw samples of chunk k landed?  (this barrier also frees the slots:
+        // every warp has finished chunk k - 1)
+        const bool ok = mbar_wait_bounded(mbar, phase);
+        phase ^= 1;
+        if (!__syncthreads_and(ok)) {
+          if (threadIdx.x == 0) atomicOr(p.err, 8);
+          timed_out = true;
+          break;
+        }
+        if (p.rf_dtype == PA_RF_F32) convert_chunk<PA_RF_F32>(p, s_cb, s_lo, smem, sbase);
+        else if (p.rf_dtype == PA_RF_BF16) convert_chunk<PA_RF_BF16>(p, s_cb, s_lo, smem, sbase);
+        else convert_chunk<PA_RF_F16>(p, s_cb, s_lo, smem, sbase);
+        __syncthreads();
+        // the raw buffer was read through the generic proxy; order that before
+        // the next asynchronous-proxy writes into it
+        if (my_cv >= 0 || threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (k + 1 < vk.y) {
+          tma_issue_chunk(p, frame, k + 1, my_cv, lo_next, s_lo, raw_s, mbar);
+          if (my_cv >= 0 && k + 2 < vk.y) lo_next = window_start(p, tile_id, k + 2, my_cv);
+        } else {
+          // last chunk: start the first chunk of the next work item now
+          const int nxt = s_item[2];
+          int pre = 0;
+          if (nxt < p.n_items) {
+            const ItemInfo ni = decode_item(p, nxt);
+            const int2 nvk = __ldg(p.vchunks + (size_t)ni.tile_id * p.ngroups + ni.grp);
+            if (nvk.x < nvk.y) {
+              const int lo = my_cv >= 0 ? window_start(p, ni.tile_id, nvk.x, my_cv) : 0;
+              tma_issue_chunk(p, ni.frame, nvk.x, my_cv, lo, s_lo, raw_s, mbar);
+              pre = 1;
+            }
+          }
+          if (threadIdx.x == 0) {
+            s_item[0] = nxt;
+            s_item[1] = pre;
+          }
+        }
+      } else {
+        __syncthreads();
+        if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+        else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+        else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+        __syncthreads();
+      }
       const int cu0 = p.u0 + k * kNC;
       int u = max(cu0, ur.x);
       const int u_end = min(cu0 + kNC, ur.y);
@@ -315,14 +502,15 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(c
       // Table entries (n0, a) [and weight] of the kC steps starting at uu.
       auto load_entries = [&](int2 (&ee)[kC], float (&ww)[kC], int uu) {
         const int r0 = row_u0 - p.m * uu;
+#ifdef PA_CHECK_BOUNDS
+        if (r0 - (kC - 1) * p.m < 0 || r0 >= p.ndrows) atomicOr(p.err, 1);
+#endif
+        const int2* tp = tcol + (size_t)r0 * p.table_stride;
+        const float* wp = APOD ? wcol + (size_t)r0 * p.table_stride : nullptr;
 #pragma unroll
         for (int tt = 0; tt < kC; ++tt) {
-#ifdef PA_CHECK_BOUNDS
-          const int rr = r0 - tt * p.m;
-          if (rr < 0 || rr >= p.ndrows) atomicOr(p.err, 1);
-#endif
-          ee[tt] = __ldg(tcol + (r0 * p.table_stride - tt * mstride));
-          if constexpr (APOD) ww[tt] = __ldg(wcol + (r0 * p.table_stride - tt * mstride));
+          ee[tt] = __ldg(tp - tt * mstride);
+          if constexpr (APOD) ww[tt] = __ldg(wp - tt * mstride);
         }
       };
       // kC channel steps x kC columns = kC^2 pairs.
@@ -376,7 +564,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(c
         block(eb, wb, u + kC);
       }
     }
+    if (timed_out) break;
     if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);
+    if (threadIdx.x == 0 && (!p.use_tma || vk.x >= vk.y)) {
+      s_item[0] = s_item[2];
+      s_item[1] = 0;
+    }
 
     // ---- FP64 Newton epilogue and store ---------------------------------
     const size_t plane = (size_t)p.nx * p.nz;
@@ -402,6 +595,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value)) k_bf_fused(c
         if (p.plane_ho >= 0) p.out[px + (size_t)p.plane_ho * plane] = ho;
       }
     }
+    __syncthreads();  // s_item is rewritten before the next item starts
   }
 }
 

@@ -2,6 +2,7 @@
 // the HO-DMAS beamformer (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,14 +21,31 @@ constexpr int kNCS = kNC + kC - 1;
 // Channel steps between Kahan folds of the compensated power sums.
 constexpr int kFoldBlocks = 2;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
-// Shared-memory layout of the fused kernel: 16 B work-item word, channel
-// bases (>= kNCS + 1 ints, multiple of 4), then the staged slots.
+// Shared-memory layout of the fused kernel: work-item words and the TMA
+// mbarrier (16 B), channel bases and window starts (kCbInts ints each,
+// >= kNCS + 1, multiple of 4), the raw TMA buffer (128-byte aligned, empty
+// without TMA), then the interpolation slots.
 constexpr int kCbInts = 40;
-constexpr int kPairsOff = 16 + kCbInts * 4;
+constexpr int kMbarOff = 16;
+constexpr int kCbOff = 32;
+constexpr int kLoOff = kCbOff + kCbInts * 4;
+constexpr int kRawOff = 384;
 constexpr int kMaxThreads = 1024;
 
+// Delay-table layout: row t = d - dmin (lattice offset d), depth z fastest,
+// so a warp's 32 depth rows read one contiguous 256-byte run per step.
+__host__ __device__ __forceinline__ size_t table_index(int t, int z, int nzp) {
+  return (size_t)t * nzp + z;
+}
+
 // Parameters of the fused gather + interpolate + root + power-sum kernel.
-struct BfParams {
+struct alignas(64) BfParams {
+  CUtensorMap tmap;       // 3-D RF map [frames][N][Ns], box {wr, 1, 1} (TMA path)
+  int use_tma;            // 1: stage with TMA boxes, 0: vectorised loads
+  int wr;                 // raw samples per channel delivered by one TMA box
+  int rp;                 // row pitch of the raw buffer in samples (128-byte rows)
+  int chunk_bytes;        // bytes one chunk's TMA boxes deliver
+  int pairs_off;          // byte offset of the interpolation slots
   const void* rf;         // [frames][N][Ns] in rf_dtype
   int rf_dtype;           // pa_rf_dtype
   int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
@@ -36,6 +54,8 @@ struct BfParams {
   const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}
   const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)
   int table_stride;       // nz_pad
+  const int4* items;      // [n_tiles * ngroups] {tile_id, grp, tx, tz}, deepest first
+  const int2* slot_rg;    // [slots] {column residue r_m, column group g}
   int ndrows;
   int dmin;               // lattice offset of table row 0
   int m;                  // pitch / dx

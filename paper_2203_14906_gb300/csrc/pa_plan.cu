@@ -6,9 +6,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "pa_internal.cuh"
 
@@ -61,6 +64,11 @@ struct pa_plan_s {
   int u0 = 0, u1 = 0, nv = 0, dmin = 0, ndrows = 0, window = 0;
   size_t smem = 0;
   int blocks_per_sm = 0;
+  bool use_tma = false;
+  int lo_align = 4;   // window starts are multiples of this many samples
+  int wr = 0;         // raw samples per channel delivered by one TMA box
+  int rp = 0;         // raw-buffer row pitch in samples (128-byte aligned rows)
+  int pairs_off = 0;  // shared-memory offset of the interpolation slots
   // post
   int M = 1, log2M = 0, post_wpb = 1, n_out = 0;
   int out_id[3] = {-1, -1, -1};  // output slot (0..n_out) of DAS, DMAS, HO
@@ -72,6 +80,8 @@ struct pa_plan_s {
   int* lo = nullptr;
   int2* urange = nullptr;
   int2* vchunks = nullptr;
+  int4* items = nullptr;   // work-item table (tile, group, tx, tz)
+  int2* slot_rg = nullptr; // warp slot -> (column residue, column group)
   float2* tw = nullptr;
   float* mask = nullptr;
   int* scratch[2] = {nullptr, nullptr};  // [err, counter, maxslots...]
@@ -135,7 +145,8 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   // n0 = -1 (taps -1, 0) moves to -2, n0 = Ns-1 (taps Ns-1, Ns) moves to Ns.
   if (n0 == -1) n0 = -2;
   if (n0 == g.ns - 1) n0 = g.ns;
-  table[(size_t)row * g.nzp + z] = make_int2(n0 * 8, __float_as_int((float)a));
+  const size_t ti = table_index(row, z, g.nzp);
+  table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
   if (wtab) {
     float w = 0.f;
     const double half = zp / (2.0 * g.fnum);
@@ -143,7 +154,7 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
       const double cw = cos(3.14159265358979323846 * dxv / (2.0 * half));
       w = (float)(cw * cw);
     }
-    wtab[(size_t)row * g.nzp + z] = w;
+    wtab[ti] = w;
   }
 }
 
@@ -154,7 +165,8 @@ struct TileGeom {
 // First staged sample (rounded down to a multiple of 4) and window width of
 // every (tile, virtual channel).  The delay grows with depth for z > 0, so the
 // minimum over the tile is on its first row and the maximum on its last.
-__global__ void k_windows(TileGeom g, const int2* table, int* lo, int* wmax, int* err) {
+__global__ void k_windows(TileGeom g, int lo_align, const int2* table, int* lo, int* wmax,
+                          int* err) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int tile = blockIdx.y;
   if (v >= g.nv) return;
@@ -169,10 +181,10 @@ __global__ void k_windows(TileGeom g, const int2* table, int* lo, int* wmax, int
       atomicOr(err, 4);
       continue;
     }
-    mn = min(mn, table[(size_t)row * g.nzp + zf].x >> 3);
-    mx = max(mx, table[(size_t)row * g.nzp + zl].x >> 3);
+    mn = min(mn, table[table_index(row, zf, g.nzp)].x >> 3);
+    mx = max(mx, table[table_index(row, zl, g.nzp)].x >> 3);
   }
-  const int lo_al = mn & ~3;
+  const int lo_al = mn & ~(lo_align - 1);  // lo_align is a power of two
   lo[(size_t)tile * g.nv + v] = lo_al;
   atomicMax(wmax, mx - lo_al + 1);
 }
@@ -195,7 +207,7 @@ __global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wt
     for (int u = g.u0; u < u1; ++u) {
       const int row = jt - g.m * u - g.dmin;
       if (row < 0 || row >= g.ndrows) continue;
-      if (wtab[(size_t)row * g.nzp + zl] > 0.f) {
+      if (wtab[table_index(row, zl, g.nzp)] > 0.f) {
         ua = min(ua, u);
         ub = max(ub, u + 1);
       }
@@ -225,7 +237,7 @@ __global__ void k_count_active(int nx, int nz, int n, int m, int dmin, int nzp,
   if (z < nz) {
     for (int i = 0; i < n; ++i) {
       const int row = j - m * i - dmin;
-      if (wtab[(size_t)row * nzp + z] > 0.f) ++c;
+      if (wtab[table_index(row, z, nzp)] > 0.f) ++c;
     }
   }
   for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(0xffffffffu, c, s);
@@ -328,6 +340,11 @@ void configure(pa_plan_s* P) {
   int B = 1;
   for (int b = 1; b <= 8; ++b)
     if (P->slots % b == 0) B = b;
+  if (B == 1) {  // prime m > 8: pair up column groups so a block has two warps
+    P->R *= 2;
+    P->slots *= 2;
+    B = 2;
+  }
   P->warps = B;
   P->ngroups = P->slots / B;
   P->threads = 32 * B;
@@ -360,17 +377,43 @@ void configure(pa_plan_s* P) {
   for (int o = 0; o < 3; ++o) P->out_id[o] = (d.outputs >> o & 1u) ? s++ : -1;
   P->dyn_range = d.dyn_range_db > 0 ? (float)d.dyn_range_db : 60.f;
   P->elt = d.rf_dtype == PA_RF_F32 ? 4 : 2;
+  // TMA boxes start on 16-byte boundaries: window starts are multiples of
+  // 16 / elt samples, and rows must be 16-byte strided.
+  P->lo_align = (int)(16 / P->elt);
+  // Measured on GB300: TMA staging wins for 16-bit RF (half-size raw buffer),
+  // vectorised loads win for FP32 RF (the FP32 raw buffer costs a resident
+  // block per SM).  PA_STAGING=tma|loads overrides the choice.
+  P->use_tma = (d.n_samples % P->lo_align) == 0 && P->elt == 2;
+  const char* staging = getenv("PA_STAGING");
+  if (staging && strcmp(staging, "loads") == 0) P->use_tma = false;
+  if (staging && strcmp(staging, "tma") == 0) P->use_tma = (d.n_samples % P->lo_align) == 0;
   if (P->d.max_batch <= 0) P->d.max_batch = 1;
 }
 
 size_t table_bytes(const pa_plan_s* P) {
-  size_t b = (size_t)P->ndrows * P->nz_pad * sizeof(int2);
-  if (P->apod) b += (size_t)P->ndrows * P->nz_pad * sizeof(float);
+  const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
+  size_t b = tab_n * sizeof(int2);
+  if (P->apod) b += tab_n * sizeof(float);
+  b += (size_t)P->n_tiles * P->ngroups * sizeof(int4) + (size_t)P->slots * sizeof(int2);
   b += (size_t)P->n_tiles * P->nv * sizeof(int);
   b += (size_t)P->n_tiles * P->slots * sizeof(int2);
   b += (size_t)P->n_tiles * P->ngroups * sizeof(int2);
   b += (size_t)P->M * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
   return b;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
 }
 
 template <typename T>
@@ -397,6 +440,8 @@ void free_plan(pa_plan_s* P) {
   cudaFree(P->lo);
   cudaFree(P->urange);
   cudaFree(P->vchunks);
+  cudaFree(P->items);
+  cudaFree(P->slot_rg);
   cudaFree(P->tw);
   cudaFree(P->mask);
   cudaFree(P->scratch[0]);
@@ -428,8 +473,11 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   PA_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
 
   pa_status s;
-  if ((s = dalloc(P, &P->table, (size_t)P->ndrows * P->nz_pad)) != PA_OK) return s;
-  if (P->apod && (s = dalloc(P, &P->wtab, (size_t)P->ndrows * P->nz_pad)) != PA_OK) return s;
+  const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
+  if ((s = dalloc(P, &P->table, tab_n)) != PA_OK) return s;
+  if (P->apod && (s = dalloc(P, &P->wtab, tab_n)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->items, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->slot_rg, (size_t)P->slots)) != PA_OK) return s;
   if ((s = dalloc(P, &P->lo, (size_t)P->n_tiles * P->nv)) != PA_OK) return s;
   if ((s = dalloc(P, &P->urange, (size_t)P->n_tiles * P->slots)) != PA_OK) return s;
   if ((s = dalloc(P, &P->vchunks, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
@@ -478,7 +526,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   int* wmax = P->scratch[0] + 2;  // borrowed before first use as image maxima
   {
     dim3 grid((P->nv + 127) / 128, P->n_tiles);
-    k_windows<<<grid, 128, 0, st>>>(g, P->table, P->lo, wmax, P->scratch[0]);
+    k_windows<<<grid, 128, 0, st>>>(g, P->lo_align, P->table, P->lo, wmax, P->scratch[0]);
     PA_CUDA(cudaGetLastError());
   }
   {
@@ -538,9 +586,28 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   P->active_pairs = P->apod ? (int64_t)active : (int64_t)d.nx * d.nz * d.n_elem;
   PA_CUDA(cudaMemcpyAsync(P->vchunks, vk.data(), vk.size() * sizeof(int2), cudaMemcpyHostToDevice,
                           st));
+  // work items (tile, residue group) deepest tiles first; the frame is the
+  // fastest index of a work item, so frames of one tile run back to back
+  std::vector<int4> it((size_t)P->n_tiles * P->ngroups);
+  for (int t = 0; t < P->n_tiles; ++t) {
+    const int tz = P->nzt - 1 - t / P->nxt, tx = t % P->nxt;
+    for (int gr = 0; gr < P->ngroups; ++gr)
+      it[(size_t)t * P->ngroups + gr] = make_int4(tz * P->nxt + tx, gr, tx, tz);
+  }
+  std::vector<int2> srg(P->slots);
+  for (int sl = 0; sl < P->slots; ++sl) srg[sl] = make_int2(sl % P->m, sl / P->m);
+  PA_CUDA(cudaMemcpyAsync(P->items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  PA_CUDA(cudaMemcpyAsync(P->slot_rg, srg.data(), srg.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                          st));
 
   // shared memory and occupancy of the fused kernel
-  P->smem = kPairsOff + (size_t)kNCS * P->window * sizeof(float2);
+  P->wr = ((P->window + 1 + P->lo_align - 1) / P->lo_align) * P->lo_align;
+  if (P->wr > 256) P->use_tma = false;  // TMA boxes span at most 256 elements
+  if (P->use_tma && !tensor_map_encoder()) P->use_tma = false;
+  P->rp = (int)((((size_t)P->wr * P->elt + 127) & ~size_t(127)) / P->elt);
+  const size_t raw_bytes = P->use_tma ? (size_t)kNCS * P->rp * P->elt : 0;
+  P->pairs_off = kRawOff + (int)((raw_bytes + 127) & ~size_t(127));
+  P->smem = (size_t)P->pairs_off + (size_t)kNCS * P->window * sizeof(float2);
   if (P->smem > 200 * 1024)
     return fail(PA_EUNSUPPORTED,
                 "RF window of %d samples per channel needs %zu B of shared memory; use a finer "
@@ -611,8 +678,23 @@ struct ChunkLaunch {
   size_t zero_ints = 0;
 };
 
-void prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
-                   int* scratch, ChunkLaunch* c) {
+bool encode_rf_map(pa_plan_s* P, const void* rf, int nf, CUtensorMap* map) {
+  const pa_plan_desc& d = P->d;
+  const cuuint64_t dims[3] = {(cuuint64_t)d.n_samples, (cuuint64_t)d.n_elem, (cuuint64_t)nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.n_samples * P->elt,
+                                 (cuuint64_t)d.n_samples * d.n_elem * P->elt};
+  const cuuint32_t box[3] = {(cuuint32_t)P->wr, 1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      P->elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  return tensor_map_encoder()(map, dt, 3, const_cast<void*>(rf), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                        int* scratch, ChunkLaunch* c) {
   const pa_plan_desc& d = P->d;
   const int n_st = popcount3(stages);
   const int planes = n_st * P->n_out;
@@ -625,6 +707,14 @@ void prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t st
   c->zero_ints = 1 + (size_t)nf * P->n_out;
 
   BfParams& b = c->b;
+  memset(&b.tmap, 0, sizeof b.tmap);
+  b.use_tma = P->use_tma ? 1 : 0;
+  b.wr = P->wr;
+  b.rp = P->rp;
+  b.chunk_bytes = kNCS * P->wr * (int)P->elt;
+  b.pairs_off = P->pairs_off;
+  if (P->use_tma && !encode_rf_map(P, rf, nf, &b.tmap))
+    return fail(PA_ECUDA, "cuTensorMapEncodeTiled rejected the RF layout");
   b.rf = rf;
   b.rf_dtype = (int)d.rf_dtype;
   b.vec_ok = (d.n_samples % 4) == 0;
@@ -634,6 +724,8 @@ void prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t st
   b.table = P->table;
   b.wtab = P->wtab;
   b.table_stride = P->nz_pad;
+  b.items = P->items;
+  b.slot_rg = P->slot_rg;
   b.ndrows = P->ndrows;
   b.dmin = P->dmin;
   b.m = P->m;
@@ -697,6 +789,7 @@ void prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t st
   l.dyn_range_db = P->dyn_range;
   l.n_frames = nf;
   log_spec(l, P->num_sms, &c->sl);
+  return PA_OK;
 }
 
 pa_status launch_direct(pa_plan_s* P, ChunkLaunch& c, cudaStream_t st) {
@@ -791,7 +884,8 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
 pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
                     cudaStream_t st, int* scratch) {
   ChunkLaunch c;
-  prepare_chunk(P, rf, nf, out, stages, scratch, &c);
+  pa_status ps = prepare_chunk(P, rf, nf, out, stages, scratch, &c);
+  if (ps != PA_OK) return ps;
   if (P->use_graph && !P->prof) return launch_graph(P, c, nf, stages, st);
   return launch_direct(P, c, st);
 }
@@ -900,6 +994,7 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->active_pairs = P->active_pairs;
   info->executed_pairs = P->executed_pairs;
   info->device_bytes = P->device_bytes;
+  info->tma_staging = P->use_tma ? 1 : 0;
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);

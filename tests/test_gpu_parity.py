@@ -27,6 +27,7 @@ def test_cfg1_all_seeds_batched_k3():
     rf = _frames(wl, wl["seeds"])
     out, info, deq = run_gpu(wl, rf, 3)
     assert info["device_error_flags"] == 0
+    assert info["tma_staging"] == 0  # FP32 RF: vectorised-load staging by default
     res = compare(out, oracle_frames(wl, deq, 3))
     assert_parity(res, TOL32, what="cfg1 k=3")
 
@@ -57,6 +58,7 @@ def test_ragged_grid_odd_aperture_unaligned_samples():
     for k in (3, 4):
         out, info, deq = run_gpu(wl, rf, k, max_batch=1)
         assert info["lattice_m"] == 2
+        assert info["tma_staging"] == 0  # Ns % 4 != 0: vectorised-load staging
         assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"ragged k={k}")
 
 
@@ -87,6 +89,8 @@ def test_apodised_cfg5_frames_bf16():
     wl = synth.workload("cfg5")
     rf = np.stack([synth.make_frame(wl, 41, f) for f in range(2)])
     out, info, deq = run_gpu(wl, rf, 4, rf_dtype="bf16", compensated=1)
+    assert info["tma_staging"] == 1  # 16-bit RF: TMA staging by default
+    assert info["device_error_flags"] == 0
     assert info["active_pairs"] < info["nominal_pairs"]
     assert info["executed_pairs"] < info["nominal_pairs"]
     ref_deq = oracle_frames(wl, deq, 4)
@@ -196,3 +200,18 @@ def test_graph_launch_matches_direct_launch():
         torch.cuda.synchronize()
     assert torch.equal(direct, g1) and torch.equal(direct, g2)
     assert torch.equal(direct[1:], g3)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_tma_and_load_staging_agree(dtype, monkeypatch):
+    """Both RF staging paths (TMA boxes, vectorised loads) give the same bits."""
+    wl = synth.workload("cfg2", nx=256, nz=256, z1_m=20e-3)
+    rf = _frames(wl, [11, 12])
+    outs = {}
+    for st in ("tma", "loads"):
+        monkeypatch.setenv("PA_STAGING", st)
+        out, info, _ = run_gpu(wl, rf, 5, rf_dtype=dtype, compensated=int(dtype != "f32"))
+        assert info["tma_staging"] == (st == "tma")
+        assert info["device_error_flags"] == 0
+        outs[st] = out
+    assert np.array_equal(outs["tma"], outs["loads"])
