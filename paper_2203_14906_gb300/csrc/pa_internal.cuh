@@ -89,7 +89,8 @@ struct PostParams {
   int n_out;           // outputs per stage
   int s_src, s_dst;    // stage index holding raw / receiving the envelope
   int nx, nz, m, log2m;
-  const float2* tw;    // [m] e^{-2 pi i k / m}
+  const float2* tw;    // per-pass twiddle blocks (see twiddles() in pa_post.cu)
+  int n_tw;            // entries of tw
   const float* mask;   // [n_out][m] band-pass x analytic mask
   int* maxslot;        // [frames][n_out] float bits of the image maximum
   int n_frames;
@@ -114,6 +115,7 @@ struct LaunchSpec {
 
 const void* bf_func(int order, bool apod, bool comp);
 void post_spec(const PostParams& p, LaunchSpec* s);
+int post_buffers(int m);  // M-point complex buffers per warp of the post kernel
 void log_spec(const LogParams& p, int num_sms, LaunchSpec* s);
 
 // Launchers (one translation unit per order keeps the builds parallel).

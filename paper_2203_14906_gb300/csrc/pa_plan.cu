@@ -70,7 +70,7 @@ struct pa_plan_s {
   int rp = 0;         // raw-buffer row pitch in samples (128-byte aligned rows)
   int pairs_off = 0;  // shared-memory offset of the interpolation slots
   // post
-  int M = 1, log2M = 0, post_wpb = 1, n_out = 0;
+  int M = 1, log2M = 0, post_wpb = 1, n_out = 0, n_tw = 0;
   int out_id[3] = {-1, -1, -1};  // output slot (0..n_out) of DAS, DMAS, HO
   uint32_t warnings = 0;
   float dyn_range = 60.f;
@@ -370,8 +370,24 @@ void configure(pa_plan_s* P) {
     ++P->log2M;
   }
   // twiddles + three M-point complex buffers per warp (two columns per warp)
-  P->post_wpb = std::max(
-      1, std::min(8, (int)(65536 / (3 * (P->M + P->M / 8) * (int)sizeof(float2)))));
+  // warps per post block: most resident warps per SM for the shared memory
+  // each needs (post_buffers padded M-point buffers per warp + the twiddles)
+  {
+    const size_t per_warp = (size_t)post_buffers(P->M) * (P->M + P->M / 8) * sizeof(float2);
+    const size_t tw = (size_t)P->M * (sizeof(float2) + sizeof(float));  // twiddles + mask
+    const size_t sm_bytes = 227 * 1024;
+    int best = 1;
+    size_t best_warps = 0;
+    for (int w = 1; w <= 8; ++w) {
+      const size_t blk = w * per_warp + tw + 1024;
+      const size_t warps = (sm_bytes / blk) * w;
+      if (blk <= 200 * 1024 && warps > best_warps) {
+        best_warps = warps;
+        best = w;
+      }
+    }
+    P->post_wpb = best;
+  }
   P->n_out = popcount3(d.outputs);
   int s = 0;
   for (int o = 0; o < 3; ++o) P->out_id[o] = (d.outputs >> o & 1u) ? s++ : -1;
@@ -398,7 +414,7 @@ size_t table_bytes(const pa_plan_s* P) {
   b += (size_t)P->n_tiles * P->nv * sizeof(int);
   b += (size_t)P->n_tiles * P->slots * sizeof(int2);
   b += (size_t)P->n_tiles * P->ngroups * sizeof(int2);
-  b += (size_t)P->M * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
+  b += (size_t)2 * P->M * sizeof(float2) + (size_t)3 * P->M * sizeof(float);
   return b;
 }
 
@@ -481,7 +497,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   if ((s = dalloc(P, &P->lo, (size_t)P->n_tiles * P->nv)) != PA_OK) return s;
   if ((s = dalloc(P, &P->urange, (size_t)P->n_tiles * P->slots)) != PA_OK) return s;
   if ((s = dalloc(P, &P->vchunks, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
-  if ((s = dalloc(P, &P->tw, (size_t)P->M)) != PA_OK) return s;
+  if ((s = dalloc(P, &P->tw, (size_t)2 * P->M)) != PA_OK) return s;  // >= n_tw
   if ((s = dalloc(P, &P->mask, (size_t)3 * P->M)) != PA_OK) return s;
   P->scratch_ints = 2 + (size_t)P->d.max_batch * 3;
   if ((s = dalloc(P, &P->scratch[0], P->scratch_ints)) != PA_OK) return s;
@@ -619,11 +635,25 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
                 P->threads, P->smem);
 
   // post-filter tables (host FP64 -> FP32)
-  std::vector<float2> tw((size_t)P->M);
-  for (int k = 0; k < P->M; ++k) {
-    const double ang = -2.0 * M_PI * (double)k / (double)P->M;
-    tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  // per-pass twiddle blocks of the Stockham FFT, in the order the passes run
+  std::vector<float2> tw;
+  {
+    int ns = 1, rem = P->log2M;
+    while (rem > 0) {
+      const int lr = rem >= 3 ? 3 : rem;
+      const int R = 1 << lr;
+      if (ns > 1)
+        for (int k = 0; k < ns; ++k)
+          for (int r = 1; r < R; ++r) {
+            const double ang = -2.0 * M_PI * (double)r * k / (double)(ns * R);
+            tw.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+          }
+      ns *= R;
+      rem -= lr;
+    }
+    if (tw.empty()) tw.push_back(make_float2(1.f, 0.f));
   }
+  P->n_tw = (int)tw.size();
   std::vector<float> mk((size_t)3 * P->M, 0.f);
   const bool even_of[3] = {false, true, (P->K % 2) == 0};
   for (int o = 0; o < 3; ++o) {
@@ -773,6 +803,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   q.m = P->M;
   q.log2m = P->log2M;
   q.tw = P->tw;
+  q.n_tw = P->n_tw;
   q.mask = P->mask;
   q.maxslot = scratch + 2;
   q.n_frames = nf;

@@ -82,44 +82,54 @@ __device__ __forceinline__ void dft_regs(float2 (&x)[R]) {
 // free of multi-way bank conflicts.
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
 
-// Twiddles W^(r k) for r = 1..R-1 from three table reads (W^k, W^2k, W^4k)
-// and products of them.
+// Twiddle tables are stored per pass in access order: the pass over
+// sub-transforms of length ns (> 1) with radix R owns ns (R - 1) entries,
+// entry k (R - 1) + r - 1 = e^{-2 pi i r k / (ns R)}.  A group reads its
+// R - 1 twiddles from consecutive addresses.
 template <int R>
-__device__ __forceinline__ void twiddles(const float2* tw, int m, int idx, float2 (&w)[R]) {
-  w[1] = tw[idx];
-  if constexpr (R >= 4) {
-    w[2] = tw[(2 * idx) & (m - 1)];
-    w[3] = cmul(w[1], w[2]);
-  }
-  if constexpr (R == 8) {
-    w[4] = tw[(4 * idx) & (m - 1)];
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-  }
+__device__ __forceinline__ void twiddles(const float2* twp, int k, float2 (&w)[R]) {
+  const float2* t = twp + k * (R - 1);
+#pragma unroll
+  for (int r = 1; r < R; ++r) w[r] = t[r - 1];
 }
 
 // One Stockham pass of radix R over sub-transforms of length ns.
 template <int R>
 __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int m, int ns,
-                                              const float2* tw, int lane) {
+                                              const float2* twp, int lane) {
   const int groups = m / R;
-  const int tw_step = m / (ns * R);
+  // With groups a multiple of 8, pidx(j + r groups) = pidx(j) + r (groups +
+  // groups / 8); with ns = 1 or a multiple of 8 the same holds for the
+  // stores.  (Both hold for every pass once M >= 64.)
+  const bool strided = (groups & 7) == 0 && (ns == 1 || (ns & 7) == 0);
+  const int is = groups + (groups >> 3), os = ns + (ns >> 3);
   for (int j = lane; j < groups; j += 32) {
     const int k = j & (ns - 1);
     float2 x[R];
+    if (strided) {
+      const float2* ip = in + pidx(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = in[pidx(j + r * groups)];
+      for (int r = 0; r < R; ++r) x[r] = ip[r * is];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = in[pidx(j + r * groups)];
+    }
     if (ns > 1) {
       float2 w[R];
-      twiddles<R>(tw, m, k * tw_step, w);
+      twiddles<R>(twp, k, w);
 #pragma unroll
       for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
     }
     dft_regs<R>(x);
     const int base = (j - k) * R + k;
+    if (strided) {
+      float2* op = out + pidx(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[pidx(base + r * ns)] = x[r];
+      for (int r = 0; r < R; ++r) op[r * os] = x[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) out[pidx(base + r * ns)] = x[r];
+    }
   }
 }
 
@@ -130,17 +140,21 @@ __device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, c
   float2* in = buf_a;
   float2* out = buf_b;
   int ns = 1, rem = log2m;
+  const float2* twp = tw;  // per-pass twiddle blocks, in pass order
   while (rem > 0) {
     if (rem >= 3) {
-      stockham_pass<8>(in, out, m, ns, tw, lane);
+      stockham_pass<8>(in, out, m, ns, twp, lane);
+      if (ns > 1) twp += ns * 7;
       ns *= 8;
       rem -= 3;
     } else if (rem == 2) {
-      stockham_pass<4>(in, out, m, ns, tw, lane);
+      stockham_pass<4>(in, out, m, ns, twp, lane);
+      if (ns > 1) twp += ns * 3;
       ns *= 4;
       rem -= 2;
     } else {
-      stockham_pass<2>(in, out, m, ns, tw, lane);
+      stockham_pass<2>(in, out, m, ns, twp, lane);
+      if (ns > 1) twp += ns;
       ns *= 2;
       rem -= 1;
     }
@@ -152,6 +166,182 @@ __device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, c
   return in;
 }
 
+// In-place Stockham pass: each lane first reads the R inputs of all its
+// groups into registers, the warp synchronises, then the outputs overwrite
+// the same buffer.  MPL = M / 32 complex values per lane (64 <= M <= 1024).
+template <int R, int MPL>
+__device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns, const float2* twp,
+                                                      int lane) {
+  constexpr int GPL = MPL >= R ? MPL / R : 1;  // groups per lane
+  const int groups = m / R;
+  const int is = groups + (groups >> 3), os = ns + (ns >> 3);
+  const bool strided = (groups & 7) == 0 && (ns == 1 || (ns & 7) == 0);
+  float2 x[GPL][R];
+#pragma unroll
+  for (int t = 0; t < GPL; ++t) {
+    const int j = lane + 32 * t;
+    if (j < groups) {
+      if (strided) {
+        const float2* ip = buf + pidx(j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[t][r] = ip[r * is];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[t][r] = buf[pidx(j + r * groups)];
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < GPL; ++t) {
+    const int j = lane + 32 * t;
+    if (j < groups) {
+      const int k = j & (ns - 1);
+      if (ns > 1) {
+        float2 w[R];
+        twiddles<R>(twp, k, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[t][r] = cmul(x[t][r], w[r]);
+      }
+      dft_regs<R>(x[t]);
+      const int base = (j - k) * R + k;
+      if (strided) {
+        float2* op = buf + pidx(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) op[r * os] = x[t][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pidx(base + r * ns)] = x[t][r];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <int MPL>
+__device__ void fft_inplace(float2* buf, int m, int log2m, const float2* tw, int lane) {
+  int ns = 1, rem = log2m;
+  const float2* twp = tw;  // per-pass twiddle blocks, in pass order
+  while (rem > 0) {
+    if (rem >= 3) {
+      stockham_pass_inplace<8, MPL>(buf, m, ns, twp, lane);
+      if (ns > 1) twp += ns * 7;
+      ns *= 8;
+      rem -= 3;
+    } else if (rem == 2) {
+      stockham_pass_inplace<4, MPL>(buf, m, ns, twp, lane);
+      if (ns > 1) twp += ns * 3;
+      ns *= 4;
+      rem -= 2;
+    } else {
+      stockham_pass_inplace<2, MPL>(buf, m, ns, twp, lane);
+      if (ns > 1) twp += ns;
+      ns *= 2;
+      rem -= 1;
+    }
+  }
+}
+
+// Envelope of one column from its transformed buffer, merged into the
+// column maximum.
+__device__ __forceinline__ void emit_env(const float2* Y, float* col, int nz, bool vec, float inv_m,
+                                         int lane, float& mx) {
+  if (vec) {
+    for (int n = 4 * lane; n < nz; n += 128) {
+      float e[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 y = Y[pidx(n + t)];
+        e[t] = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
+        mx = fmaxf(mx, e[t]);
+      }
+      *reinterpret_cast<float4*>(col + n) = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  } else {
+    for (int n = lane; n < nz; n += 32) {
+      const float2 y = Y[pidx(n)];
+      const float env = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
+      col[n] = env;
+      mx = fmaxf(mx, env);
+    }
+  }
+}
+
+// k_post for 64 <= M <= 1024: two M-point buffers per warp (in-place FFTs).
+// Same algorithm as k_post below: pack two real columns, forward FFT, split
+// the spectra with the conjugate symmetry, mask, conjugate, forward FFT of
+// each half, modulus / M.
+template <int MPL>
+__global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
+  extern __shared__ __align__(16) float2 sbuf[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int M = 32 * MPL;
+  constexpr int MP = M + (M >> 3);
+  float2* tw = sbuf;  // p.n_tw per-pass twiddles, then the mask, then buffers
+  float* mk = reinterpret_cast<float*>(sbuf + p.n_tw);
+  for (int k = threadIdx.x; k < p.n_tw; k += blockDim.x) tw[k] = __ldg(p.tw + k);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) mk[k] = __ldg(p.mask + (size_t)blockIdx.y * M + k);
+  __syncthreads();
+  const int j0 = 2 * (blockIdx.x * p.warps_per_block + warp);
+  const int o = blockIdx.y, f = blockIdx.z;
+  if (j0 >= p.nx) return;  // no block barrier below
+  const bool two = j0 + 1 < p.nx;
+  float2* A = sbuf + p.n_tw + M / 2 + (size_t)warp * 2 * MP;
+  float2* B = A + MP;
+  const size_t plane = (size_t)p.nx * p.nz;
+  const float* src = p.out + ((size_t)f * p.planes + (size_t)p.s_src * p.n_out + o) * plane +
+                     (size_t)j0 * p.nz;
+  float* dst = p.out + ((size_t)f * p.planes + (size_t)p.s_dst * p.n_out + o) * plane +
+               (size_t)j0 * p.nz;
+  const bool vec = (p.nz & 3) == 0;
+  if (vec) {
+    for (int n = 4 * lane; n < M; n += 128) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (n < p.nz) {
+        a = *reinterpret_cast<const float4*>(src + n);
+        if (two) b = *reinterpret_cast<const float4*>(src + p.nz + n);
+      }
+      A[pidx(n)] = make_float2(a.x, b.x);
+      A[pidx(n + 1)] = make_float2(a.y, b.y);
+      A[pidx(n + 2)] = make_float2(a.z, b.z);
+      A[pidx(n + 3)] = make_float2(a.w, b.w);
+    }
+  } else {
+    for (int n = lane; n < M; n += 32) {
+      const bool in_col = n < p.nz;
+      const float a = in_col ? src[n] : 0.f;
+      const float b = (in_col && two) ? src[p.nz + n] : 0.f;
+      A[pidx(n)] = make_float2(a, b);
+    }
+  }
+  __syncwarp();
+  fft_inplace<MPL>(A, M, p.log2m, tw, lane);
+  for (int k = lane; k <= M / 2; k += 32) {
+    const int km = (M - k) & (M - 1);
+    const float2 z = A[pidx(k)], zc = A[pidx(km)];
+    const float hk = 0.5f * mk[k];
+    B[pidx(k)] = make_float2(hk * (z.x + zc.x), -hk * (z.y - zc.y));
+    A[pidx(k)] = make_float2(hk * (z.y + zc.y), hk * (z.x - zc.x));
+    if (km != k) {
+      const float hm = 0.5f * mk[km];
+      B[pidx(km)] = make_float2(hm * (zc.x + z.x), -hm * (zc.y - z.y));
+      A[pidx(km)] = make_float2(hm * (zc.y + z.y), hm * (zc.x - z.x));
+    }
+  }
+  __syncwarp();
+  const float inv_m = 1.0f / (float)M;
+  float mx = 0.f;
+  fft_inplace<MPL>(B, M, p.log2m, tw, lane);
+  emit_env(B, dst, p.nz, vec, inv_m, lane, mx);
+  if (two) {
+    fft_inplace<MPL>(A, M, p.log2m, tw, lane);
+    emit_env(A, dst + p.nz, p.nz, vec, inv_m, lane, mx);
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+  if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
+}
+
 // Shared memory: the M-entry twiddle table, then three M-point complex
 // buffers per warp.
 __global__ void __launch_bounds__(256) k_post(const PostParams p) {
@@ -159,14 +349,14 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = p.m;
   const int MP = M + (M >> 3);  // padded buffer length
-  float2* tw = sbuf;
-  for (int k = threadIdx.x; k < M; k += blockDim.x) tw[k] = __ldg(p.tw + k);
+  float2* tw = sbuf;  // p.n_tw per-pass twiddles, then the buffers
+  for (int k = threadIdx.x; k < p.n_tw; k += blockDim.x) tw[k] = __ldg(p.tw + k);
   __syncthreads();
   const int j0 = 2 * (blockIdx.x * p.warps_per_block + warp);
   const int o = blockIdx.y, f = blockIdx.z;
   if (j0 >= p.nx) return;  // no block barrier below
   const bool two = j0 + 1 < p.nx;
-  float2* b0 = sbuf + M + (size_t)warp * 3 * MP;
+  float2* b0 = sbuf + p.n_tw + (size_t)warp * 3 * MP;
   float2* b1 = b0 + MP;
   float2* b2 = b1 + MP;
   const size_t plane = (size_t)p.nx * p.nz;
@@ -284,14 +474,35 @@ __global__ void __launch_bounds__(256) k_log(const LogParams p) {
   }
 }
 
+const void* post_inplace_func(int m);
+
 cudaError_t post_configure(size_t smem) {
-  return cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (int m = 64; m <= 1024 && e == cudaSuccess; m *= 2)
+    e = cudaFuncSetAttribute(post_inplace_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  return e;
 }
+
+const void* post_inplace_func(int m) {
+  switch (m) {
+    case 64: return reinterpret_cast<const void*>(k_post_inplace<2>);
+    case 128: return reinterpret_cast<const void*>(k_post_inplace<4>);
+    case 256: return reinterpret_cast<const void*>(k_post_inplace<8>);
+    case 512: return reinterpret_cast<const void*>(k_post_inplace<16>);
+    case 1024: return reinterpret_cast<const void*>(k_post_inplace<32>);
+  }
+  return nullptr;
+}
+
+int post_buffers(int m) { return post_inplace_func(m) ? 2 : 3; }
 
 void post_spec(const PostParams& p, LaunchSpec* ls) {
   const size_t mp = (size_t)p.m + (p.m >> 3);
-  ls->func = reinterpret_cast<const void*>(k_post);
-  ls->smem = ((size_t)p.warps_per_block * 3 * mp + p.m) * sizeof(float2);
+  const void* f = post_inplace_func(p.m);
+  ls->func = f ? f : reinterpret_cast<const void*>(k_post);
+  ls->smem = ((size_t)p.warps_per_block * post_buffers(p.m) * mp + p.n_tw) * sizeof(float2) +
+             (f ? (size_t)p.m * sizeof(float) : 0);
   const int col_pairs = (p.nx + 1) / 2;
   ls->grid = dim3((col_pairs + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
   ls->block = dim3(p.warps_per_block * 32);
@@ -313,8 +524,8 @@ void log_spec(const LogParams& p, int num_sms, LaunchSpec* ls) {
 cudaError_t post_launch(const PostParams& p, cudaStream_t s) {
   LaunchSpec ls;
   post_spec(p, &ls);
-  k_post<<<ls.grid, ls.block, ls.smem, s>>>(p);
-  return cudaGetLastError();
+  void* args[] = {const_cast<PostParams*>(&p)};
+  return cudaLaunchKernel(ls.func, ls.grid, ls.block, args, ls.smem, s);
 }
 
 cudaError_t log_launch(const LogParams& p, int num_sms, cudaStream_t s) {
