@@ -94,6 +94,28 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+# ------------------------------------------------------------- multi-rank
+def rank_frames(rank: int, frames_per_rank: int):
+    """Frame indices of one rank: replicas over frames, no overlap."""
+    return list(range(rank * frames_per_rank, (rank + 1) * frames_per_rank))
+
+
+def max_over_ranks(t: float, pg, device=None) -> float:
+    """Slowest rank's time (the job's time)."""
+    if pg is None:
+        return t
+    import torch
+
+    x = torch.tensor([t], dtype=torch.float64, device=device)
+    pg.all_reduce(x, op=pg.ReduceOp.MAX)
+    return float(x.item())
+
+
+def job_value(pairs_per_rank_step: float, world: int, steps: int, t_max: float) -> float:
+    """Whole-job Gpixel.ch/s: every rank's pairs over the slowest rank's time."""
+    return pairs_per_rank_step * world * steps / t_max / 1e9
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons (200 ms period)."""
@@ -391,7 +413,7 @@ def run_ours(args):
     wl = workload()
     F, k = args.frames, args.order
     pairs_step = wl["nx"] * wl["nz"] * wl["n_elem"] * F
-    frames64 = np.stack([synth.make_frame(wl, 11, rank * F + f) for f in range(F)])
+    frames64 = np.stack([synth.make_frame(wl, 11, f) for f in rank_frames(rank, F)])
     stream = torch.cuda.Stream(dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -411,12 +433,8 @@ def run_ours(args):
     times, prof, info = time_form(pa, torch, wl, args, "f32", 0, frames64, stream, flush)
     clocks = clk.stop()
     barrier()
-    t_tot = sum(times)
-    if pg is not None:
-        t = torch.tensor([t_tot], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_tot = float(t.item())
-    value = pairs_step * ws * args.steps / t_tot / 1e9
+    t_tot = max_over_ranks(sum(times), pg, dev)
+    value = job_value(pairs_step, ws, args.steps, t_tot)
 
     # roofline of the dominant kernel (the fused beamformer)
     bf_ms, bf_n = prof["bf_fused"]
@@ -451,11 +469,8 @@ def run_ours(args):
         for _ in range(e2e_steps):
             pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
         te = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([te], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": pairs_step * ws * e2e_steps / te / 1e9, "unit": UNIT,
+    te = max_over_ranks(te, pg, dev)
+    e2e = {"value": job_value(pairs_step, ws, e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": int(rf_h.numel() * rf_h.element_size()),
            "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size()),
            "call": "pa_beamform_host (pinned host buffers)", "steps": e2e_steps}
