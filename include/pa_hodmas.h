@@ -57,6 +57,12 @@ typedef enum {
 
 typedef enum { PA_RF_F32 = 0, PA_RF_BF16 = 1, PA_RF_F16 = 2 } pa_rf_dtype;
 
+/* Sampling of the delayed signal.  LINEAR interpolates between the two
+ * samples around the delay; NEAREST takes the sample at the rounded delay,
+ * s_i[k + Delta_i] with an integer index exactly as Eq. 1 writes it (valid
+ * iff 0 <= round(tau) <= Ns-1, rounding halves up). */
+typedef enum { PA_INTERP_LINEAR = 0, PA_INTERP_NEAREST = 1 } pa_interp;
+
 /* Output images (bit mask).  Planes of one frame are ordered DAS, DMAS,
  * HODMAS, keeping only the requested ones. */
 enum { PA_OUT_DAS = 1u, PA_OUT_DMAS = 2u, PA_OUT_HODMAS = 4u };
@@ -86,6 +92,7 @@ typedef struct {
   double band_hi_hz;     /* < 0: band-pass off (analytic mask only)         */
   double dyn_range_db;   /* log-compression range; <= 0 means 60 dB        */
   int32_t compensated;   /* 1: Kahan-compensated FP32 power sums            */
+  pa_interp interp;      /* sampling of the delayed signal                  */
 } pa_plan_desc;
 
 typedef struct pa_plan_s* pa_plan_t;
@@ -298,7 +305,7 @@ const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);
 /* ABI version (major * 100 + minor). */
-int32_t pa_version(void);
+int32_t pa_version(void);  /* 101: pa_plan_desc.interp */
 
 #ifdef __cplusplus
 }

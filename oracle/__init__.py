@@ -56,6 +56,7 @@ class Desc(ctypes.Structure):
         ("band_lo_hz", ctypes.c_double),
         ("band_hi_hz", ctypes.c_double),
         ("dyn_range_db", ctypes.c_double),
+        ("nearest", ctypes.c_int32),
     ]
 
 
@@ -95,6 +96,7 @@ def lib():
             "or_pix_z": (d, [D, i]),
             "or_delay": (d, [D, i, i, i]),
             "or_lerp": (d, [pd, i, d]),
+            "or_nearest": (d, [pd, i, d]),
             "or_apod": (d, [D, i, i, i]),
             "or_root": (d, [d, i]),
             "or_power_sums": (None, [pd, i, i, pd]),
@@ -155,6 +157,7 @@ def desc(wl: dict, order_k=None) -> Desc:
         band_lo_hz=float(wl.get("band_lo_hz", 0.0)),
         band_hi_hz=float(wl.get("band_hi_hz", 0.0)),
         dyn_range_db=float(wl.get("dyn_range_db", 60.0)),
+        nearest=int(wl.get("interp", "linear") == "nearest"),
     )
 
 
@@ -207,6 +210,11 @@ def delay(wl, i, j, l):
 def lerp(row, tau):
     row = _f64(row)
     return float(lib().or_lerp(_pd(row), row.size, float(tau)))
+
+
+def nearest(row, tau):
+    row = _f64(row)
+    return float(lib().or_nearest(_pd(row), row.size, float(tau)))
 
 
 def apod(wl, i, j, l):

@@ -53,6 +53,17 @@ double or_lerp(const double* row, int ns, double tau) {
   return row[n0] + a * (row[n0 + 1] - row[n0]);
 }
 
+double or_nearest(const double* row, int ns, double tau) {
+  double n = floor(tau + 0.5);
+  if (n < 0.0 || n > (double)(ns - 1)) return 0.0;
+  return row[(int)n];
+}
+
+double or_sample(const or_desc* d, const double* row, double tau) {
+  return d->nearest ? or_nearest(row, d->n_samples, tau)
+                    : or_lerp(row, d->n_samples, tau);
+}
+
 double or_apod(const or_desc* d, int i, int j, int l) {
   if (d->f_number <= 0.0) return 1.0;
   double z = or_pix_z(d, l);
@@ -192,7 +203,7 @@ static void pixel(const or_desc* d, const double* rf, int j, int l,
   int n = d->n_elem, ns = d->n_samples;
   for (int i = 0; i < n; ++i) {
     double tau = or_delay(d, i, j, l);
-    double s = or_lerp(rf + (int64_t)i * ns, ns, tau);
+    double s = or_sample(d, rf + (int64_t)i * ns, tau);
     s_buf[i] = or_apod(d, i, j, l) * s;
   }
   if (das) *das = or_paper_form(s_buf, n, 1);
@@ -240,7 +251,7 @@ void or_beamform_bruteforce(const or_desc* d, const double* rf, double* ho) {
     for (int l = 0; l < d->nz; ++l) {
       for (int i = 0; i < n; ++i) {
         double tau = or_delay(d, i, j, l);
-        s[i] = or_apod(d, i, j, l) * or_lerp(rf + (int64_t)i * ns, ns, tau);
+        s[i] = or_apod(d, i, j, l) * or_sample(d, rf + (int64_t)i * ns, tau);
       }
       ho[(int64_t)j * d->nz + l] = or_bruteforce(s, n, d->order_k);
     }

@@ -37,6 +37,7 @@ typedef struct {
   double band_lo_hz;   /* <=0 (with band_hi>=0): parity-dependent default    */
   double band_hi_hz;   /* <0: band-pass off (analytic mask only)            */
   double dyn_range_db; /* log-compression dynamic range                      */
+  int32_t nearest;     /* 1: integer delays as Eq. 1 writes them (no interp.) */
 } or_desc;
 
 /* ---- geometry and delay (Eq. 1 and Section 2.1) ---- */
@@ -48,6 +49,12 @@ double or_delay(const or_desc* d, int i, int j, int l);
 /* Linear interpolation of row[] at fractional index tau; 0 when either tap
  * lies outside [0, ns-1] (such a channel contributes nothing). */
 double or_lerp(const double* row, int ns, double tau);
+/* Nearest sample of row[] at fractional index tau: the integer delay of
+ * Eq. 1, n = floor(tau + 1/2) (halves round up); 0 unless 0 <= n <= ns-1. */
+double or_nearest(const double* row, int ns, double tau);
+/* The delayed sample of one channel: or_nearest when d->nearest, else
+ * or_lerp. */
+double or_sample(const or_desc* d, const double* row, double tau);
 /* Dynamic-aperture Hann weight (1 when f_number <= 0). */
 double or_apod(const or_desc* d, int i, int j, int l);
 

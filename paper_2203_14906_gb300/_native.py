@@ -20,6 +20,8 @@ PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EUNSUPPORTED, PA_EBUSY = 
 PA_RF_F32, PA_RF_BF16, PA_RF_F16 = 0, 1, 2
 PA_OUT_DAS, PA_OUT_DMAS, PA_OUT_HODMAS = 1, 2, 4
 PA_STAGE_RAW, PA_STAGE_ENV, PA_STAGE_LOG = 1, 2, 4
+PA_INTERP_LINEAR, PA_INTERP_NEAREST = 0, 1
+INTERPS = {"linear": PA_INTERP_LINEAR, "nearest": PA_INTERP_NEAREST}
 
 RF_DTYPES = {"f32": PA_RF_F32, "bf16": PA_RF_BF16, "f16": PA_RF_F16}
 
@@ -64,6 +66,7 @@ class PlanDesc(ctypes.Structure):
         ("band_hi_hz", ctypes.c_double),
         ("dyn_range_db", ctypes.c_double),
         ("compensated", ctypes.c_int32),
+        ("interp", ctypes.c_int32),
     ]
 
 
@@ -176,6 +179,7 @@ def make_desc(wl: dict, order_k=None, outputs=7, rf_dtype=None, max_batch=1,
         band_hi_hz=float(wl.get("band_hi_hz", 0.0)),
         dyn_range_db=float(wl.get("dyn_range_db", 60.0)),
         compensated=int(wl.get("compensated", 0) if compensated is None else compensated),
+        interp=INTERPS[wl.get("interp", "linear")],
     )
 
 

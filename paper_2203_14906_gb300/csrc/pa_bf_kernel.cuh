@@ -23,6 +23,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "pa_internal.cuh"
 
 namespace pa {
@@ -513,8 +515,10 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
           if constexpr (APOD) ww[tt] = __ldg(wp - tt * mstride);
         }
       };
-      // kC channel steps x kC columns = kC^2 pairs.
-      auto block = [&](const int2 (&ee)[kC], const float (&ww)[kC], int uu) {
+      // kC channel steps x kC columns = kC^2 pairs.  NEAR: nearest-sample
+      // delays (Eq. 1), one tap per pair and no interpolation.
+      auto block = [&](auto near_tag, const int2 (&ee)[kC], const float (&ww)[kC], int uu) {
+        constexpr bool NEAR = decltype(near_tag)::value;
         int cb[2 * kC];
         {
           // channel bases of channels uu .. uu + 2kC - 2 (uu - cu0 is a multiple of 4)
@@ -536,9 +540,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
               addr = pairs_off;
             }
 #endif
-            float2 r;
-            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
-            float s = fmaf(a, r.y, r.x);
+            float s;
+            if constexpr (NEAR) {
+              asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(addr));
+            } else {
+              float2 r;
+              asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
+              s = fmaf(a, r.y, r.x);
+            }
             if constexpr (APOD) s *= ww[tt];
             pair_update<K>(acc[c], s);
           }
@@ -558,10 +567,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       for (; u < u_end; u += 2 * kC) {
         const bool has_b = u + kC < u_end;
         if (has_b) load_entries(eb, wb, u + kC);
-        block(ea, wa, u);
+        if (p.nearest) block(std::true_type{}, ea, wa, u);
+        else block(std::false_type{}, ea, wa, u);
         if (!has_b) break;
         if (u + 2 * kC < u_end) load_entries(ea, wa, u + 2 * kC);
-        block(eb, wb, u + kC);
+        if (p.nearest) block(std::true_type{}, eb, wb, u + kC);
+        else block(std::false_type{}, eb, wb, u + kC);
       }
     }
     if (timed_out) break;

@@ -49,6 +49,7 @@ struct alignas(64) BfParams {
   const void* rf;         // [frames][N][Ns] in rf_dtype
   int rf_dtype;           // pa_rf_dtype
   int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
+  int nearest;            // 1: nearest-sample delays (a = 0), one tap per pair
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
   const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}

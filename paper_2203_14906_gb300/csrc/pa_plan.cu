@@ -117,7 +117,7 @@ namespace {
 
 // ---------------------------------------------------------- plan kernels
 struct TableGeom {
-  int ndrows, nzp, dmin, ns;
+  int ndrows, nzp, dmin, ns, nearest;
   double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
   double dx, z0, dz, fs, c, t0, fnum;
 };
@@ -133,8 +133,9 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   const double dxv = g.x_const + ((double)(g.dmin + row) + 0.5) * g.dx;
   const double zp = g.z0 + ((double)z + 0.5) * g.dz;
   const double tau = g.fs * (sqrt(dxv * dxv + zp * zp) / g.c - g.t0);
-  double fl = floor(tau);
-  double a = tau - fl;
+  // linear: n0 = floor(tau), a = tau - n0; nearest (Eq. 1): n0 = round(tau), a = 0
+  double fl = g.nearest ? floor(tau + 0.5) : floor(tau);
+  double a = g.nearest ? 0.0 : tau - fl;
   const double lim = 1048576.0;
   if (fl < -lim) { fl = -lim; a = 0.0; }
   if (fl > lim) { fl = lim; a = 0.0; }
@@ -143,8 +144,10 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   // samples outside [0, Ns) are zero, so pointing such delays at a slot whose
   // two taps both lie outside the record gives s = 0 with no test per pair:
   // n0 = -1 (taps -1, 0) moves to -2, n0 = Ns-1 (taps Ns-1, Ns) moves to Ns.
-  if (n0 == -1) n0 = -2;
-  if (n0 == g.ns - 1) n0 = g.ns;
+  // (With a = 0 the nearest sample reads only the first tap: slots n0 = -1 and
+  // n0 = Ns-1 already give 0 and r[Ns-1], so no remapping is needed.)
+  if (!g.nearest && n0 == -1) n0 = -2;
+  if (!g.nearest && n0 == g.ns - 1) n0 = g.ns;
   const size_t ti = table_index(row, z, g.nzp);
   table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
   if (wtab) {
@@ -307,6 +310,8 @@ pa_status validate(const pa_plan_desc* d) {
   if (d->rf_dtype != PA_RF_F32 && d->rf_dtype != PA_RF_BF16 && d->rf_dtype != PA_RF_F16)
     return fail(PA_EINVAL, "rf_dtype %d invalid", (int)d->rf_dtype);
   if (d->f_number < 0) return fail(PA_EINVAL, "f_number must be >= 0");
+  if (d->interp != PA_INTERP_LINEAR && d->interp != PA_INTERP_NEAREST)
+    return fail(PA_EINVAL, "interp %d invalid", (int)d->interp);
   if (d->f_number > 0 || d->band_hi_hz >= 0) {
     if (!(d->f0_hz > 0) && !(d->band_lo_hz > 0 && d->band_hi_hz > 0) && d->band_hi_hz >= 0)
       return fail(PA_EINVAL, "f0_hz must be positive for the default band");
@@ -513,6 +518,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   tg.nzp = P->nz_pad;
   tg.dmin = P->dmin;
   tg.ns = d.n_samples;
+  tg.nearest = d.interp == PA_INTERP_NEAREST;
   tg.dx = (d.x1_m - d.x0_m) / d.nx;
   tg.x_const = d.x0_m + 0.5 * (d.n_elem - 1) * d.pitch_m;
   tg.z0 = d.z0_m;
@@ -748,6 +754,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.rf = rf;
   b.rf_dtype = (int)d.rf_dtype;
   b.vec_ok = (d.n_samples % 4) == 0;
+  b.nearest = d.interp == PA_INTERP_NEAREST;
   b.n_elem = d.n_elem;
   b.n_samples = d.n_samples;
   b.frame_elems = (long long)d.n_elem * d.n_samples;
@@ -1179,6 +1186,6 @@ const char* pa_status_str(pa_status s) {
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int32_t pa_version(void) { return 100; }
+int32_t pa_version(void) { return 101; }
 
 }  // extern "C"

@@ -80,6 +80,10 @@ def test_validation_rejects_bad_descriptors():
     d = _native.make_desc(wl)
     d.rf_dtype = 7
     assert _status(d)[0] == _native.PA_EINVAL
+    d = _native.make_desc(wl)
+    d.interp = 2
+    assert _status(d)[0] == _native.PA_EINVAL
+    assert _status(_native.make_desc(dict(wl, interp="nearest")))[0] == _native.PA_OK
     # pitch/dx = 64 exceeds the supported lattice
     w = dict(wl, nx=64 * 64)
     assert _status(_native.make_desc(w))[0] == _native.PA_EUNSUPPORTED

@@ -174,6 +174,7 @@ def test_checked_build_raises_no_bounds_flags():
         (synth.workload("cfg1"), 3, "f32", 0),
         (synth.workload("cfg1", n_samples=300, t0_s=2e-6, nz=96), 5, "f32", 0),
         (synth.workload("cfg5", nx=256, nz=256), 4, "bf16", 1),
+        (synth.workload("cfg1", n_samples=300, t0_s=2e-6, nz=96, interp="nearest"), 3, "f32", 0),
     ]
     for wl, k, dt, comp in cases:
         rf = synth.make_frame(wl, 1)[None]
@@ -215,3 +216,54 @@ def test_tma_and_load_staging_agree(dtype, monkeypatch):
         assert info["device_error_flags"] == 0
         outs[st] = out
     assert np.array_equal(outs["tma"], outs["loads"])
+
+
+def test_long_columns_and_odd_width():
+    """nz > 1024 (2048-point envelope transforms, the out-of-place FFT path),
+    an odd number of columns (the last column pair has one column) and a
+    lattice factor of 3."""
+    wl = synth.workload("cfg1", n_elem=25, nx=75, nz=1500, n_samples=2048, z1_m=30e-3)
+    wl["x0_m"], wl["x1_m"] = -25 * 0.15e-3, 25 * 0.15e-3
+    rf = _frames(wl, [9])
+    out, info, deq = run_gpu(wl, rf, 3)
+    assert info["fft_size"] == 2048 and info["lattice_m"] == 3
+    assert_parity(compare(out, oracle_frames(wl, deq, 3)), TOL32, what="nz=1500, nx=75")
+
+
+def test_short_columns():
+    """nz < 64: envelope transforms of 32 and 8 points (out-of-place path)."""
+    for nz in (20, 7):
+        wl = synth.workload("cfg1", nx=64, nz=nz, z1_m=nz * 0.4e-3)
+        rf = _frames(wl, [6])
+        out, info, deq = run_gpu(wl, rf, 4)
+        assert_parity(compare(out, oracle_frames(wl, deq, 4)), TOL32, what=f"nz={nz}")
+
+
+@pytest.mark.parametrize("k", [1, 3, 4])
+def test_nearest_sample_delays(k):
+    """Integer delays exactly as Eq. 1 writes them (no interpolation): cfg1
+    batched, a ragged grid with short records and t0 > 0 (indices at both
+    ends of the record), and cfg5-style apodisation with BF16 RF."""
+    wl = synth.workload("cfg1", interp="nearest")
+    rf = _frames(wl, [1, 2])
+    out, info, deq = run_gpu(wl, rf, k)
+    assert info["device_error_flags"] == 0
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"nearest cfg1 k={k}")
+    wl = synth.workload("cfg1", interp="nearest", n_elem=37, n_samples=301, t0_s=1.5e-6,
+                        nx=74, nz=77, z1_m=18e-3)
+    wl["x0_m"], wl["x1_m"] = -37 * 0.15e-3, 37 * 0.15e-3
+    rf = _frames(wl, [7])
+    out, _, deq = run_gpu(wl, rf, k, max_batch=1)
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"nearest ragged k={k}")
+    wl = synth.workload("cfg5", interp="nearest", nx=256, nz=256)
+    rf = _frames(wl, [41])
+    out, info, deq = run_gpu(wl, rf, k, rf_dtype="bf16", compensated=1)
+    assert info["tma_staging"] == 1
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"nearest apod k={k}")
+
+
+def test_nearest_full_size_cfg2():
+    wl = synth.workload("cfg2", interp="nearest")
+    rf = _frames(wl, wl["seeds"][:2])
+    out, _, deq = run_gpu(wl, rf, 3)
+    assert_parity(compare(out, oracle_frames(wl, deq, 3)), TOL32, what="nearest cfg2")

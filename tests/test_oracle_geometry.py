@@ -3,7 +3,10 @@
 * Hand-computed delays on a 3-4-5 triangle geometry (Section 2.1, Eq. 1).
 * The DAS image of a delta-pulse RF frame equals the analytic sum of
   triangle functions tri(tau_i(p) - n_i) (linear interpolation of a unit
-  impulse), a sum of hyperbolic ridges.
+  impulse), a sum of hyperbolic ridges; with integer delays (Eq. 1 as
+  written) it counts the channels whose rounded delay hits the impulse.
+* Hand-computed nearest-sample values; nearest and linear sampling agree
+  wherever every delay is an exact number of samples.
 * A single on-axis point absorber images to its true pixel, and higher
   orders lower the lateral sidelobes (Section 3's qualitative claim).
 * The full-image beamformer equals the k-subset definition on tiny arrays.
@@ -39,6 +42,43 @@ def test_worked_lerp():
     g = _gold()["lerp"]
     for c in g["cases"]:
         assert oracle.lerp(g["row"], c["tau"]) == pytest.approx(c["expected"], abs=1e-12)
+
+
+def test_worked_nearest():
+    g = _gold()["nearest"]
+    for c in g["cases"]:
+        assert oracle.nearest(g["row"], c["tau"]) == c["expected"], c
+
+
+def test_nearest_is_linear_at_the_rounded_index():
+    """Away from the record's last sample, the nearest sample equals linear
+    interpolation evaluated at round(tau) (fraction 0)."""
+    rng = np.random.default_rng(3)
+    row = rng.standard_normal(50)
+    for tau in rng.uniform(-3.0, 52.0, 400):
+        n = np.floor(tau + 0.5)
+        want = oracle.lerp(row, n) if 0 <= n < 49 else (row[49] if n == 49 else 0.0)
+        assert oracle.nearest(row, tau) == want
+
+
+def test_delta_pulse_nearest_counts_hits():
+    """Integer delays (Eq. 1): the DAS image of a delta-pulse frame counts, at
+    each pixel, the channels whose rounded delay lands on the impulse."""
+    wl = synth.workload("cfg1", nx=64, nz=48, interp="nearest")
+    rf, ni = _delta_frame(wl, -0.9e-3, 9.5e-3)
+    das = oracle.beamform(wl, rf)["das"]
+    n = wl["n_elem"]
+    xe = (np.arange(n) - (n - 1) / 2.0) * wl["pitch_m"]
+    xp = wl["x0_m"] + (np.arange(wl["nx"]) + 0.5) * (wl["x1_m"] - wl["x0_m"]) / wl["nx"]
+    zp = wl["z0_m"] + (np.arange(wl["nz"]) + 0.5) * (wl["z1_m"] - wl["z0_m"]) / wl["nz"]
+    tau = wl["fs_hz"] / wl["c_m_s"] * np.sqrt(
+        (xp[:, None, None] - xe[None, None, :]) ** 2 + zp[None, :, None] ** 2
+    )
+    frac = tau - np.floor(tau)
+    assert np.min(np.abs(frac - 0.5)) > 1e-9  # no rounding ties on this grid
+    want = (np.floor(tau + 0.5) == ni[None, None, :]).sum(axis=2)
+    assert np.array_equal(das, want.astype(float))
+    assert want.max() >= 8
 
 
 def test_worked_apodisation():
