@@ -341,6 +341,67 @@ def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
     return times, prof, info
 
 
+def metrics_rois(wl):
+    """Ten target discs (r = 0.5 mm) in five depth pairs, the layout of the
+    paper's point-target phantom (Section 4), each with a 1-2 mm annulus as
+    background."""
+    w = wl["x1_m"] - wl["x0_m"]
+    h = wl["z1_m"] - wl["z0_m"]
+    rois = []
+    for fz in (0.2, 0.35, 0.5, 0.65, 0.8):
+        for fx in (-0.15, 0.15):
+            xc, zc = wl["x0_m"] + (0.5 + fx) * w, wl["z0_m"] + fz * h
+            rois.append((dict(shape="disc", xc_m=xc, zc_m=zc, a_m=0.5e-3),
+                         dict(shape="annulus", xc_m=xc, zc_m=zc, a_m=1.0e-3, b_m=2.0e-3)))
+    return rois
+
+
+def metrics_bench(pa, torch, wl, args, frames64, stream, flush):
+    """pa_image_metrics on the envelope images of one step (frames x 3
+    outputs), device-timed with an L2 flush before each call."""
+    import ctypes
+
+    import synth
+    from paper_2203_14906_gb300._native import Metrics
+
+    F = frames64.shape[0]
+    store, _ = synth.quantize(frames64, "f32")
+    rf = torch.from_numpy(store).cuda()
+    desc = pa.make_desc(wl, order_k=args.order, outputs=7, rf_dtype="f32", max_batch=F)
+    rois = metrics_rois(wl)
+    reps = max(3, min(args.steps, 50))
+    with pa.Plan(desc, stream=stream) as plan, torch.cuda.stream(stream):
+        env = pa.beamform(plan, rf, pa.PA_STAGE_ENV, stream=stream)[:, 0].contiguous()
+        n_img = env.shape[0] * env.shape[1]
+        rec = torch.empty(n_img * len(rois) * ctypes.sizeof(Metrics), dtype=torch.uint8,
+                          device=env.device)
+        for _ in range(args.warmup):
+            pa.image_metrics(env, wl, rois, stream=stream, out=rec)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for a, b in evs:
+            flush()
+            a.record(stream)
+            pa.image_metrics(env, wl, rois, stream=stream, out=rec)
+            b.record(stream)
+        stream.synchronize()
+        m = pa.image_metrics(env, wl, rois, stream=stream)
+    t = float(np.mean([a.elapsed_time(b) for a, b in evs])) / 1e3
+    # algorithmic bytes: both passes read every member pixel once (4 B each)
+    members = float(np.sum(m["n_in"]) + np.sum(m["n_out"]))
+    nbytes = 2 * 4 * members
+    return {
+        "images_per_s": n_img / t, "ms_per_call": t * 1e3, "images_per_call": n_img,
+        "roi_pairs_per_image": len(rois), "launches_per_call": 5,
+        "member_pixels_per_call": members, "algorithmic_bytes_per_call": nbytes,
+        "achieved_gbs": nbytes / t / 1e9,
+        "note": ("launch- and latency-bound, not HBM-bound: the regions cover "
+                 f"{members / n_img / (wl['nx'] * wl['nz']):.1%} of each image"),
+        "sample_hodmas_frame0": {kk: float(np.nanmean(m[kk][2])) for kk in
+                                 ("snr_db", "cr_db", "gcnr", "fwhm_m")},
+    }
+
+
 def serving_bench(pa, args, rf_dtype, comp):
     """Replay the cfg4 Poisson trace through the continuous-batching server."""
     import torch
@@ -485,12 +546,22 @@ def run_ours(args):
             "vs_fp32_form": v_bf * ws / value,
             "kernel_ms_per_launch": prof_bf["bf_fused"][0] / max(prof_bf["bf_fused"][1], 1),
         }
+        # nearest-sample delays (Eq. 1's integer index), FP32, same workload
+        wl_n = dict(wl, interp="nearest")
+        t_nn, prof_nn, _ = time_form(pa, torch, wl_n, args, "f32", 0, frames64, stream, flush)
+        v_nn = pairs_step * args.steps / sum(t_nn) / 1e9
+        extras["nearest_form"] = {
+            "value": v_nn * ws, "unit": UNIT, "interp": "nearest (Eq. 1 integer delay)",
+            "vs_fp32_form": v_nn * ws / value,
+            "kernel_ms_per_launch": prof_nn["bf_fused"][0] / max(prof_nn["bf_fused"][1], 1),
+        }
         if rank == 0:
             extras["precision_report"] = {
                 "fp32": precision_report(pa, wl, k, frames64[0], "f32", 0),
                 "bf16_kahan": precision_report(pa, wl, k, frames64[0], "bf16", 1),
                 "against": "FP64 oracle on the unquantised RF, frame 0",
             }
+            extras["metrics_form"] = metrics_bench(pa, torch, wl, args, frames64, stream, flush)
             done, v_cpu, dt, cores = oracle_run(wl, frames64, k, args.cpu_seconds)
             extras["cpu_baseline"] = {
                 "value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",

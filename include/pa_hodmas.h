@@ -268,6 +268,83 @@ pa_status pa_server_get_stats(pa_server_t srv, pa_server_stats* stats);
  * buffer.  Pending requests that never ran complete with PA_EBUSY. */
 pa_status pa_server_destroy(pa_server_t srv);
 
+/* ------------------------------------------------------------------------
+ * Image-quality metrics of Section 4 on images already in device memory:
+ * SNR (Eq. 10), CR (Eq. 11), gCNR (Eq. 12) and the lateral FWHM of a
+ * target's main lobe.  Meant for envelope images (the ENV stage, linear
+ * amplitude), which is what the paper's PA signal amplitudes are.
+ *
+ * Definitions (where the paper leaves a choice, the reading is stated):
+ *   regions   a pixel belongs to a region when its centre
+ *             (x0 + (j + 1/2) dx, z0 + (l + 1/2) dz) lies inside it, tested
+ *             in FP64 without fused multiply-adds: RECT |x - xc| <= a and
+ *             |z - zc| <= b; DISC d^2 <= a^2; ANNULUS a^2 < d^2 <= b^2,
+ *             d^2 = (x - xc)^2 + (z - zc)^2 (a disc and an annulus with the
+ *             same a partition the plane around the centre).
+ *   mu_in, mu_out   means over the target / background pixels; sigma_out the
+ *             background's population standard deviation (divides by n_out).
+ *   snr_db = 20 log10(mu_in / sigma_out), cr_db = 20 log10(mu_in / mu_out).
+ *   gcnr      1 - sum_b min(h_in[b], h_out[b]) over 256 bins of the
+ *             normalised amplitude v / vmax, vmax the largest value in the
+ *             two regions; bin = min(255, floor((v * 256) / vmax)) in FP32
+ *             with an IEEE-rounded division (values <= 0, or vmax <= 0,
+ *             fall in bin 0); h = bin count / region pixel count.
+ *   fwhm_m    on the image row (fixed depth) of the target's maximum
+ *             (first in x-major order on ties): walk left and right from it
+ *             while the value stays >= max / 2; each side's crossing is
+ *             linearly interpolated between the last pixel >= max / 2 and
+ *             the first one below; fwhm = x_right - x_left.  NaN when a side
+ *             reaches the image edge without crossing.
+ *   Undefined quantities (an empty region, 0 / 0) are NaN or +-inf as IEEE
+ *   arithmetic gives them; peak_j = peak_l = -1 for an empty target.
+ * ---------------------------------------------------------------------- */
+typedef enum { PA_REGION_RECT = 0, PA_REGION_DISC = 1, PA_REGION_ANNULUS = 2 } pa_region_shape;
+
+typedef struct {
+  int32_t shape;         /* pa_region_shape                                */
+  double xc_m, zc_m;     /* centre                                         */
+  double a_m, b_m;       /* RECT half-widths in x, z; DISC radius a;
+                            ANNULUS inner radius a, outer radius b         */
+} pa_region;
+
+typedef struct {
+  pa_region target;      /* "in" region of Eqs. 10-12                      */
+  pa_region background;  /* "out" region                                   */
+} pa_roi;
+
+typedef struct {
+  int32_t nx, nz;          /* image grid, the same as the plan's            */
+  double x0_m, x1_m;
+  double z0_m, z1_m;
+} pa_grid;
+
+typedef struct {
+  double mu_in, mu_out, sigma_out;
+  double snr_db, cr_db, gcnr, fwhm_m;
+  double peak;             /* largest target value                         */
+  int64_t n_in, n_out;     /* pixels in the target / background            */
+  int32_t peak_j, peak_l;  /* where the target maximum is                  */
+} pa_metrics;
+
+#define PA_METRICS_MAX_ROIS 4096
+/*
+ * pa_image_metrics -- every ROI pair on every image.
+ *   images_dev  [n_images][nx][nz] FP32, z fastest, device memory (e.g. the
+ *               ENV planes of pa_beamform called with stages = PA_STAGE_ENV:
+ *               n_images = frames x outputs).  Caller-owned, read only.
+ *   rois        host array of n_roi pairs (1 <= n_roi <= PA_METRICS_MAX_ROIS),
+ *               read before the call returns.
+ *   out_dev     [n_images][n_roi] pa_metrics in device memory, caller-owned.
+ * Asynchronous on cuda_stream; its scratch memory is taken from and given
+ * back to the device's default memory pool in stream order.  The result is
+ * deterministic (fixed reduction order).  n_images == 0 is a no-op.
+ * Errors: PA_EINVAL (null pointers, bad grid, n_roi out of range, unknown
+ * region shape, negative extents), PA_ENOMEM, PA_ECUDA.
+ */
+pa_status pa_image_metrics(const pa_grid* grid, const float* images_dev, int32_t n_images,
+                           const pa_roi* rois, int32_t n_roi, pa_metrics* out_dev,
+                           void* cuda_stream);
+
 /* Frees everything the plan owns after synchronising the streams it used.
  * NULL is accepted (no-op). */
 pa_status pa_destroy(pa_plan_t plan);

@@ -21,5 +21,6 @@ from ._native import (  # noqa: F401
     footprint,
     load,
     make_desc,
+    make_grid,
 )
-from .torch_api import beamform, beamform_host  # noqa: F401
+from .torch_api import beamform, beamform_host, image_metrics  # noqa: F401

@@ -35,6 +35,7 @@ EXPORTS = (
     "pa_plan_use_graph",
     "pa_plan_profile",
     "pa_plan_profile_read",
+    "pa_image_metrics",
     "pa_destroy",
     "pa_status_str",
     "pa_last_error",
@@ -100,6 +101,68 @@ class PAError(RuntimeError):
         self.status = status
 
 
+PA_REGION_RECT, PA_REGION_DISC, PA_REGION_ANNULUS = 0, 1, 2
+REGION_SHAPES = {"rect": PA_REGION_RECT, "disc": PA_REGION_DISC, "annulus": PA_REGION_ANNULUS}
+PA_METRICS_MAX_ROIS = 4096
+
+
+class Region(ctypes.Structure):
+    _fields_ = [
+        ("shape", ctypes.c_int32),
+        ("xc_m", ctypes.c_double),
+        ("zc_m", ctypes.c_double),
+        ("a_m", ctypes.c_double),
+        ("b_m", ctypes.c_double),
+    ]
+
+
+class Roi(ctypes.Structure):
+    _fields_ = [("target", Region), ("background", Region)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("x0_m", ctypes.c_double),
+        ("x1_m", ctypes.c_double),
+        ("z0_m", ctypes.c_double),
+        ("z1_m", ctypes.c_double),
+    ]
+
+
+class Metrics(ctypes.Structure):
+    _fields_ = [
+        ("mu_in", ctypes.c_double),
+        ("mu_out", ctypes.c_double),
+        ("sigma_out", ctypes.c_double),
+        ("snr_db", ctypes.c_double),
+        ("cr_db", ctypes.c_double),
+        ("gcnr", ctypes.c_double),
+        ("fwhm_m", ctypes.c_double),
+        ("peak", ctypes.c_double),
+        ("n_in", ctypes.c_int64),
+        ("n_out", ctypes.c_int64),
+        ("peak_j", ctypes.c_int32),
+        ("peak_l", ctypes.c_int32),
+    ]
+
+
+def make_region(r) -> Region:
+    """``r``: a Region, or a dict {shape: rect|disc|annulus, xc_m, zc_m, a_m, b_m}."""
+    if isinstance(r, Region):
+        return r
+    return Region(REGION_SHAPES[r["shape"]] if isinstance(r["shape"], str) else int(r["shape"]),
+                  float(r["xc_m"]), float(r["zc_m"]), float(r["a_m"]), float(r.get("b_m", 0.0)))
+
+
+def make_grid(wl) -> Grid:
+    """Image grid of a workload dict or a PlanDesc."""
+    g = (lambda k: getattr(wl, k)) if isinstance(wl, PlanDesc) else (lambda k: wl[k])
+    return Grid(int(g("nx")), int(g("nz")), float(g("x0_m")), float(g("x1_m")),
+                float(g("z0_m")), float(g("z1_m")))
+
+
 def load(checked: bool = False, build: bool = True):
     """Load (building if stale) the CUDA library; raises if unavailable."""
     key = bool(checked)
@@ -135,6 +198,9 @@ def load(checked: bool = False, build: bool = True):
         L.pa_plan_profile_read.restype = ctypes.c_int
         L.pa_log_compress_noalloc.argtypes = [vp, i32, ctypes.c_int64, ctypes.c_float, vp, vp]
         L.pa_log_compress_noalloc.restype = ctypes.c_int
+        L.pa_image_metrics.argtypes = [ctypes.POINTER(Grid), vp, i32, ctypes.POINTER(Roi), i32,
+                                       vp, vp]
+        L.pa_image_metrics.restype = ctypes.c_int
         L.pa_destroy.argtypes = [vp]
         L.pa_destroy.restype = ctypes.c_int
         L.pa_status_str.argtypes = [ctypes.c_int]

@@ -39,7 +39,7 @@ __host__ __device__ __forceinline__ size_t table_index(int t, int z, int nzp) {
 }
 
 // Parameters of the fused gather + interpolate + root + power-sum kernel.
-struct alignas(64) BfParams {
+struct BfParams {  // aligned as CUtensorMap requires
   CUtensorMap tmap;       // 3-D RF map [frames][N][Ns], box {wr, 1, 1} (TMA path)
   int use_tma;            // 1: stage with TMA boxes, 0: vectorised loads
   int wr;                 // raw samples per channel delivered by one TMA box

@@ -7,9 +7,22 @@ ABI: RF ``[frames][N][Ns]``, output ``[frames][stages][outputs][nx][nz]``.
 
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 
-from ._native import PA_RF_BF16, PA_RF_F16, PA_RF_F32, Plan
+from ._native import (
+    PA_RF_BF16,
+    PA_RF_F16,
+    PA_RF_F32,
+    Metrics,
+    Plan,
+    Roi,
+    check,
+    load,
+    make_grid,
+    make_region,
+)
 
 
 def _torch():
@@ -84,3 +97,52 @@ def beamform_host(plan: Plan, rf, stages: int, out=None, stream=None):
         optr = out.data_ptr()
     plan.beamform_host(ptr, n, optr, stages, stream)
     return out
+
+
+METRIC_FIELDS = tuple(name for name, _ in Metrics._fields_)
+
+
+def image_metrics(images, grid, rois, stream=None, out=None):
+    """SNR, CR, gCNR and lateral FWHM (Eqs. 10-12) of every ROI pair on every
+    image, computed on the device by ``pa_image_metrics``.
+
+    ``images``: CUDA float32 tensor ``[..., nx, nz]`` (leading dims are
+    flattened into the image count); ``grid``: workload dict or PlanDesc;
+    ``rois``: list of (target, background) region dicts.  Returns a dict of
+    numpy arrays shaped ``[n_images, n_roi]`` (synchronises ``stream``), or,
+    with ``out`` (a CUDA uint8 tensor of n_images * n_roi * sizeof(Metrics)
+    bytes), leaves the raw records there without synchronising."""
+    torch = _torch()
+    g = make_grid(grid)
+    if not (images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()):
+        raise ValueError("images must be a contiguous CUDA float32 tensor")
+    if tuple(images.shape[-2:]) != (g.nx, g.nz):
+        raise ValueError(f"images must end in [{g.nx}][{g.nz}]")
+    n_img = int(np.prod(images.shape[:-2])) if images.dim() > 2 else 1
+    arr = (Roi * len(rois))(*[Roi(make_region(t), make_region(b)) for t, b in rois])
+    nbytes = n_img * len(rois) * ctypes.sizeof(Metrics)
+    if out is None:
+        dev = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=images.device)
+    else:
+        dev = out
+        if dev.numel() < nbytes or not dev.is_cuda:
+            raise ValueError("out is too small")
+    if stream is None:
+        stream = torch.cuda.current_stream(images.device)
+    L = load()
+    check(L, L.pa_image_metrics(ctypes.byref(g), images.data_ptr(), n_img, arr, len(rois),
+                                dev.data_ptr(), stream.cuda_stream))
+    if out is not None:
+        return out
+    stream.synchronize()
+    host = dev[:nbytes].cpu().numpy()
+    rec = np.frombuffer(host.tobytes(), dtype=_metrics_dtype()).reshape(n_img, len(rois))
+    return {name: rec[name].copy() for name in METRIC_FIELDS}
+
+
+def _metrics_dtype():
+    fmt = {ctypes.c_double: "f8", ctypes.c_int64: "i8", ctypes.c_int32: "i4"}
+    return np.dtype({"names": list(METRIC_FIELDS),
+                     "formats": [fmt[t] for _, t in Metrics._fields_],
+                     "offsets": [getattr(Metrics, n).offset for n in METRIC_FIELDS],
+                     "itemsize": ctypes.sizeof(Metrics)})

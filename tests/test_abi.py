@@ -144,3 +144,29 @@ def test_server_config_validation_without_gpu():
     d = _native.make_desc(synth.workload("cfg1"))
     assert L.pa_server_submit(None, ctypes.byref(d), None, None, 0.0, ctypes.byref(t)) == _native.PA_EINVAL
     assert L.pa_server_destroy(None) == _native.PA_OK
+
+
+def test_metrics_validation_without_gpu():
+    """pa_image_metrics checks its arguments before touching the device."""
+    L = _native.load()
+    g = _native.make_grid(dict(nx=16, nz=16, x0_m=0.0, x1_m=1e-3, z0_m=0.0, z1_m=1e-3))
+    reg = _native.make_region
+    roi = (_native.Roi * 1)(_native.Roi(reg(dict(shape="disc", xc_m=0, zc_m=0, a_m=1e-4)),
+                                        reg(dict(shape="annulus", xc_m=0, zc_m=0, a_m=1e-4,
+                                                 b_m=3e-4))))
+    call = lambda grid, n_img, rois, n_roi: L.pa_image_metrics(  # noqa: E731
+        ctypes.byref(grid), None, n_img, rois, n_roi, None, None)
+    assert call(g, 0, roi, 1) == _native.PA_OK  # nothing to do
+    assert call(g, 1, roi, 0) == _native.PA_EINVAL
+    assert call(g, 1, roi, _native.PA_METRICS_MAX_ROIS + 1) == _native.PA_EINVAL
+    assert call(g, 1, roi, 1) == _native.PA_EINVAL  # null image / output buffers
+    assert b"null buffer" in L.pa_last_error()
+    bad = (_native.Roi * 1)(_native.Roi(_native.Region(7, 0, 0, 1e-4, 0), roi[0].background))
+    assert call(g, 1, bad, 1) == _native.PA_EINVAL
+    neg = (_native.Roi * 1)(_native.Roi(reg(dict(shape="disc", xc_m=0, zc_m=0, a_m=-1.0)),
+                                        roi[0].background))
+    assert call(g, 1, neg, 1) == _native.PA_EINVAL
+    g.x1_m = g.x0_m
+    assert call(g, 1, roi, 1) == _native.PA_EINVAL
+    assert L.pa_image_metrics(None, None, 1, roi, 1, None, None) == _native.PA_EINVAL
+    assert ctypes.sizeof(_native.Metrics) == 88
