@@ -121,6 +121,8 @@ typedef struct {
                                   TMA wait that ran out (the kernel stopped
                                   early).  Reading it synchronises the
                                   device.                                  */
+  int32_t chunk_steps;        /* channel steps staged per shared-memory
+                                 chunk of the fused kernel                 */
 } pa_plan_info;
 
 /*
@@ -382,7 +384,7 @@ const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);
 /* ABI version (major * 100 + minor). */
-int32_t pa_version(void);  /* 101: pa_plan_desc.interp */
+int32_t pa_version(void);  /* 102: pa_plan_info.chunk_steps */
 
 #ifdef __cplusplus
 }

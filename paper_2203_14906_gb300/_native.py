@@ -89,6 +89,7 @@ class PlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("tma_staging", ctypes.c_int32),
         ("device_error_flags", ctypes.c_uint32),
+        ("chunk_steps", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -9,7 +9,7 @@
 //            m = pitch / dx.  At channel step u, pixel c pairs with channel
 //            i = u + c and all kC pairs share the lattice offset
 //            d = jt - m u, so one delay-table entry (n0, a) serves kC pairs.
-//   chunk  = kNC channel steps; the RF sample window of every channel the
+//   chunk  = nc channel steps (per plan); the RF sample window of every channel the
 //            chunk touches is staged in shared memory as overlapping FP32
 //            pairs (r[n], r[n+1]) so one 64-bit LDS fetches both
 //            interpolation taps.  Slots outside [0, Ns-2] hold zeros, which
@@ -174,7 +174,7 @@ __device__ __forceinline__ void rf_load4(const void* rf, size_t idx, float* r) {
 
 static_assert(kC == 4, "channel-base loads below read 2 x int4");
 
-// Stage the sample windows of virtual channels [v0, v0 + kNCS) of one tile.
+// Stage the sample windows of virtual channels [v0, v0 + ncs) of one tile.
 // Slot q of staged channel cv holds (r[n], r[n+1] - r[n]) for n = lo + q, so
 // the interpolated sample is one FMA, s = r[n] + a (r[n+1] - r[n]); samples
 // outside [0, Ns) (and virtual channels) are zero.  The plan-time table never
@@ -190,12 +190,12 @@ __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int ti
   const int ns = p.n_samples;
   const int* lo_t = p.lo + (size_t)tile_id * p.nv;
   const size_t frame_base = (size_t)frame * p.n_elem;
-  if (threadIdx.x < kNCS) {
-    const int v = v0 + threadIdx.x;
+  for (int c = threadIdx.x; c < p.ncs; c += blockDim.x) {
+    const int v = v0 + c;
     const int lo = v < p.nv ? __ldg(lo_t + v) : 0;
-    s_cb[threadIdx.x] = (int)sbase + p.pairs_off + (int)threadIdx.x * W * 8 - lo * 8;
+    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - lo * 8;
   }
-  const int total = kNCS * W4;
+  const int total = p.ncs * W4;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
     const int q = idx - cv * W4;
@@ -268,19 +268,19 @@ __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, in
       : "memory");
 }
 
-// The boxes of a chunk are issued by kNCS threads spread over the warps
-// (staged channel cv = lane * nwarps + warp; blocks have at least two warps,
-// so ceil(kNCS / nwarps) <= 18 lanes per warp suffice), so no warp falls
-// behind the others; each issuing thread keeps its channel's next window
-// start in a register, loaded one chunk ahead.
-__device__ __forceinline__ int tma_channel() {
+// The boxes of a chunk are issued by ncs threads spread over the warps
+// (staged channel cv = lane * nwarps + warp; the plan keeps ncs <= 32 nwarps,
+// so every staged channel has an issuing lane), so no warp falls behind the
+// others; each issuing thread keeps its channel's next window start in a
+// register, loaded one chunk ahead.
+__device__ __forceinline__ int tma_channel(int ncs) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cv = lane * nwarps + warp;
-  return (lane * nwarps < kNCS && cv < kNCS) ? cv : -1;
+  return cv < ncs ? cv : -1;
 }
 
 __device__ __forceinline__ int window_start(const BfParams& p, int tile_id, int k, int cv) {
-  const int v = k * kNC + cv;
+  const int v = k * p.nc + cv;
   return v < p.nv ? __ldg(p.lo + (size_t)tile_id * p.nv + v) : 0;
 }
 
@@ -291,7 +291,7 @@ __device__ __forceinline__ void tma_issue_chunk(const BfParams& p, int frame, in
   if (cv >= 0) {
     const int elt = p.rf_dtype == PA_RF_F32 ? 4 : 2;
     s_lo[cv] = lo;
-    tma_box(raw_s + (uint32_t)(cv * p.rp * elt), &p.tmap, lo, k * kNC + cv + p.u0, frame, mbar);
+    tma_box(raw_s + (uint32_t)(cv * p.rp * elt), &p.tmap, lo, k * p.nc + cv + p.u0, frame, mbar);
   }
 }
 
@@ -300,9 +300,9 @@ template <int DT>
 __device__ __forceinline__ void convert_chunk(const BfParams& p, int* s_cb, const int* s_lo,
                                               unsigned char* smem, uint32_t sbase) {
   const int W = p.window, W4 = W >> 2;
-  if (threadIdx.x < kNCS)
-    s_cb[threadIdx.x] = (int)sbase + p.pairs_off + (int)threadIdx.x * W * 8 - s_lo[threadIdx.x] * 8;
-  const int total = kNCS * W4;
+  for (int c = threadIdx.x; c < p.ncs; c += blockDim.x)
+    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - s_lo[c] * 8;
+  const int total = p.ncs * W4;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
     const int q = idx - cv * W4;
@@ -386,14 +386,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
   int* s_lo = reinterpret_cast<int*>(smem + kLoOff);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t mbar = sbase + kMbarOff;
-  const int my_cv = tma_channel();
+  const int my_cv = tma_channel(p.ncs);
   const uint32_t raw_s = sbase + kRawOff;
   const int pairs_off = (int)sbase + p.pairs_off;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
 #ifdef PA_CHECK_BOUNDS
-  const int smem_hi = pairs_off + kNCS * p.window * 8 - 8;  // shared addresses
+  const int smem_hi = pairs_off + p.ncs * p.window * 8 - 8;  // shared addresses
 #endif
   int phase = 0;
   if (threadIdx.x == 0) {
@@ -491,14 +491,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         }
       } else {
         __syncthreads();
-        if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
-        else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
-        else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * kNC, s_cb, smem, sbase);
+        if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
+        else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
+        else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
         __syncthreads();
       }
-      const int cu0 = p.u0 + k * kNC;
+      const int cu0 = p.u0 + k * p.nc;
       int u = max(cu0, ur.x);
-      const int u_end = min(cu0 + kNC, ur.y);
+      const int u_end = min(cu0 + p.nc, ur.y);
       if (u >= u_end) continue;
 
       // Table entries (n0, a) [and weight] of the kC steps starting at uu.

@@ -15,21 +15,23 @@ namespace pa {
 // need the delay of the same lattice offset d = jt - m*u (pixel c pairs with
 // channel i = u + c): one table load serves kC pairs.
 constexpr int kC = 4;
-// Channel steps per shared-memory chunk and virtual channels staged per chunk.
-constexpr int kNC = 32;
-constexpr int kNCS = kNC + kC - 1;
+// Channel steps per shared-memory chunk (chosen per plan, a multiple of kC,
+// at most kNCMax) and the virtual channels staged per chunk (steps + kC - 1).
+constexpr int kNCMax = 72;
+constexpr int kNCSMax = kNCMax + kC - 1;
 // Channel steps between Kahan folds of the compensated power sums.
 constexpr int kFoldBlocks = 2;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
 // Shared-memory layout of the fused kernel: work-item words and the TMA
 // mbarrier (16 B), channel bases and window starts (kCbInts ints each,
-// >= kNCS + 1, multiple of 4), the raw TMA buffer (128-byte aligned, empty
+// >= kNCSMax + 1, multiple of 4), the raw TMA buffer (128-byte aligned, empty
 // without TMA), then the interpolation slots.
-constexpr int kCbInts = 40;
+constexpr int kCbInts = 76;
 constexpr int kMbarOff = 16;
 constexpr int kCbOff = 32;
 constexpr int kLoOff = kCbOff + kCbInts * 4;
-constexpr int kRawOff = 384;
+constexpr int kRawOff = 640;  // >= kLoOff + 4 kCbInts, 128-byte aligned
+static_assert(kRawOff >= kLoOff + kCbInts * 4 && kRawOff % 128 == 0, "shared layout");
 constexpr int kMaxThreads = 1024;
 
 // Delay-table layout: row t = d - dmin (lattice offset d), depth z fastest,
@@ -50,6 +52,7 @@ struct BfParams {  // aligned as CUtensorMap requires
   int rf_dtype;           // pa_rf_dtype
   int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
   int nearest;            // 1: nearest-sample delays (a = 0), one tap per pair
+  int nc, ncs;            // channel steps per chunk, virtual channels staged per chunk
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
   const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}

@@ -66,6 +66,7 @@ struct pa_plan_s {
   int blocks_per_sm = 0;
   bool use_tma = false;
   int lo_align = 4;   // window starts are multiples of this many samples
+  int nc = 32;        // channel steps per staged chunk (multiple of kC)
   int wr = 0;         // raw samples per channel delivered by one TMA box
   int rp = 0;         // raw-buffer row pitch in samples (128-byte aligned rows)
   int pairs_off = 0;  // shared-memory offset of the interpolation slots
@@ -585,6 +586,56 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   P->window = ((std::max(width, 1) + 3) / 4) * 4;
   PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
 
+  // TMA box geometry of one staged channel
+  P->wr = ((P->window + 1 + P->lo_align - 1) / P->lo_align) * P->lo_align;
+  if (P->wr > 256) P->use_tma = false;  // TMA boxes span at most 256 elements
+  if (P->use_tma && !tensor_map_encoder()) P->use_tma = false;
+  P->rp = (int)((((size_t)P->wr * P->elt + 127) & ~size_t(127)) / P->elt);
+  // Chunk length: every chunk costs a staging pass and two block barriers,
+  // so the channel steps are cut into as few, evenly sized chunks as keep
+  // the fused kernel's occupancy at what 32-step chunks give (measured at
+  // N = 128: 5 chunks of 28 steps 0.696 ms, 4 of 36 0.692 ms, 3 of 44
+  // 0.678 ms).  Limits: the slot buffer (at most 200 KiB), one issuing lane
+  // per staged channel under TMA (ncs <= 32 warps), and the multiply-shift
+  // division of the staging loops (exact while ncs * (W/4)^2 < 2^20).
+  // PA_CHUNK_STEPS caps the chunk length (for measurements).
+  {
+    const int steps = P->u1 - P->u0;
+    auto smem_for = [&](int c) {
+      const int ncs = c + kC - 1;
+      const size_t raw = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
+      return (size_t)kRawOff + ((raw + 127) & ~size_t(127)) + (size_t)ncs * P->window * 8;
+    };
+    auto fits = [&](int c) {
+      const int ncs = c + kC - 1;
+      const long long w4 = P->window / 4;
+      return smem_for(c) <= 200 * 1024 && ncs <= 32 * P->warps &&
+             (long long)ncs * w4 * w4 < (1ll << 20);
+    };
+    auto occupancy = [&](int c) {
+      int b = 0;
+      if (bf_occupancy(P->K, P->apod, P->comp, P->threads, smem_for(c), &b) != cudaSuccess) b = 0;
+      return b;
+    };
+    auto even = [&](int nch) { return ((steps + nch - 1) / nch + kC - 1) / kC * kC; };
+    int cap = kNCMax;
+    if (const char* e = getenv("PA_CHUNK_STEPS")) cap = std::max(kC, std::min(kNCMax, atoi(e)));
+    int ref = std::min(32, cap);
+    while (ref > kC && !fits(ref)) ref -= kC;
+    const int occ_ref = occupancy(ref);
+    int nc = ref;
+    for (int nch = (steps + cap - 1) / cap; nch <= (steps + ref - 1) / ref; ++nch) {
+      const int c = std::min(even(nch), cap);
+      if (c > ref && fits(c) && occupancy(c) >= occ_ref) {
+        nc = c;
+        break;
+      }
+    }
+    if (nc == ref) nc = std::min(ref, even((steps + ref - 1) / ref));
+    P->nc = nc;
+  }
+  cudaGetLastError();
+
   // tile chunk ranges and executed pairs
   std::vector<int2> vk((size_t)P->n_tiles * P->ngroups);
   int64_t exec = 0;
@@ -600,7 +651,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
         }
       }
       int2 c = make_int2(0, 0);
-      if (ub > ua) c = make_int2((ua - P->u0) / kNC, (ub - P->u0 + kNC - 1) / kNC);
+      if (ub > ua) c = make_int2((ua - P->u0) / P->nc, (ub - P->u0 + P->nc - 1) / P->nc);
       vk[(size_t)t * P->ngroups + gr] = c;
     }
   }
@@ -623,13 +674,14 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
                           st));
 
   // shared memory and occupancy of the fused kernel
-  P->wr = ((P->window + 1 + P->lo_align - 1) / P->lo_align) * P->lo_align;
-  if (P->wr > 256) P->use_tma = false;  // TMA boxes span at most 256 elements
-  if (P->use_tma && !tensor_map_encoder()) P->use_tma = false;
-  P->rp = (int)((((size_t)P->wr * P->elt + 127) & ~size_t(127)) / P->elt);
-  const size_t raw_bytes = P->use_tma ? (size_t)kNCS * P->rp * P->elt : 0;
+  const int ncs = P->nc + kC - 1;
+  const size_t raw_bytes = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
   P->pairs_off = kRawOff + (int)((raw_bytes + 127) & ~size_t(127));
-  P->smem = (size_t)P->pairs_off + (size_t)kNCS * P->window * sizeof(float2);
+  P->smem = (size_t)P->pairs_off + (size_t)ncs * P->window * sizeof(float2);
+  const long long w4 = P->window / 4;
+  if ((long long)ncs * w4 * w4 >= (1ll << 20))
+    return fail(PA_EUNSUPPORTED, "RF window of %d samples per channel is too wide; use a finer "
+                "depth grid", P->window);
   if (P->smem > 200 * 1024)
     return fail(PA_EUNSUPPORTED,
                 "RF window of %d samples per channel needs %zu B of shared memory; use a finer "
@@ -747,7 +799,9 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.use_tma = P->use_tma ? 1 : 0;
   b.wr = P->wr;
   b.rp = P->rp;
-  b.chunk_bytes = kNCS * P->wr * (int)P->elt;
+  b.nc = P->nc;
+  b.ncs = P->nc + kC - 1;
+  b.chunk_bytes = b.ncs * P->wr * (int)P->elt;
   b.pairs_off = P->pairs_off;
   if (P->use_tma && !encode_rf_map(P, rf, nf, &b.tmap))
     return fail(PA_ECUDA, "cuTensorMapEncodeTiled rejected the RF layout");
@@ -1033,6 +1087,7 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->executed_pairs = P->executed_pairs;
   info->device_bytes = P->device_bytes;
   info->tma_staging = P->use_tma ? 1 : 0;
+  info->chunk_steps = P->nc;
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);
@@ -1186,6 +1241,6 @@ const char* pa_status_str(pa_status s) {
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int32_t pa_version(void) { return 101; }
+int32_t pa_version(void) { return 102; }
 
 }  // extern "C"

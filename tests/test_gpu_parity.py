@@ -267,3 +267,25 @@ def test_nearest_full_size_cfg2():
     rf = _frames(wl, wl["seeds"][:2])
     out, _, deq = run_gpu(wl, rf, 3)
     assert_parity(compare(out, oracle_frames(wl, deq, 3)), TOL32, what="nearest cfg2")
+
+
+def test_chunk_length_does_not_change_bits(monkeypatch):
+    """The channel steps staged per shared-memory chunk (plan policy, or the
+    PA_CHUNK_STEPS override) change only the staging schedule: every pixel
+    still sums its channels in the same order, so the images are identical.
+    FP32 loads staging and BF16 TMA staging, with and without apodisation."""
+    wl = synth.workload("cfg1", n_elem=128, nx=256, nz=96, z1_m=12e-3)
+    wl["x0_m"], wl["x1_m"] = -128 * 0.15e-3, 128 * 0.15e-3
+    rf = _frames(wl, [3, 4])
+    wa = synth.workload("cfg5", nx=256, nz=128)
+    ra = _frames(wa, [41])
+    for w, r, k, dt, comp in ((wl, rf, 3, "f32", 0), (wl, rf, 5, "bf16", 1), (wa, ra, 4, "bf16", 1)):
+        monkeypatch.delenv("PA_CHUNK_STEPS", raising=False)
+        ref, info, _ = run_gpu(w, r, k, rf_dtype=dt, compensated=comp)
+        assert info["chunk_steps"] % 4 == 0 and info["chunk_steps"] <= 64
+        for steps in ("4", "32", "64"):
+            monkeypatch.setenv("PA_CHUNK_STEPS", steps)
+            out, info2, _ = run_gpu(w, r, k, rf_dtype=dt, compensated=comp)
+            assert info2["chunk_steps"] <= int(steps)
+            assert info2["device_error_flags"] == 0
+            assert np.array_equal(out, ref), (w["name"], k, dt, steps)
