@@ -218,59 +218,153 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
   __syncwarp();
 }
 
-template <int MPL>
-__device__ void fft_inplace(float2* buf, int m, int log2m, const float2* tw, int lane) {
-  int ns = 1, rem = log2m;
-  const float2* twp = tw;  // per-pass twiddle blocks, in pass order
-  while (rem > 0) {
-    if (rem >= 3) {
-      stockham_pass_inplace<8, MPL>(buf, m, ns, twp, lane);
-      if (ns > 1) twp += ns * 7;
-      ns *= 8;
-      rem -= 3;
-    } else if (rem == 2) {
-      stockham_pass_inplace<4, MPL>(buf, m, ns, twp, lane);
-      if (ns > 1) twp += ns * 3;
-      ns *= 4;
-      rem -= 2;
-    } else {
-      stockham_pass_inplace<2, MPL>(buf, m, ns, twp, lane);
-      if (ns > 1) twp += ns;
-      ns *= 2;
-      rem -= 1;
-    }
-  }
-}
-
-// Envelope of one column from its transformed buffer, merged into the
-// column maximum.
-__device__ __forceinline__ void emit_env(const float2* Y, float* col, int nz, bool vec, float inv_m,
-                                         int lane, float& mx) {
-  if (vec) {
-    for (int n = 4 * lane; n < nz; n += 128) {
-      float e[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const float2 y = Y[pidx(n + t)];
-        e[t] = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
-        mx = fmaxf(mx, e[t]);
-      }
-      *reinterpret_cast<float4*>(col + n) = make_float4(e[0], e[1], e[2], e[3]);
-    }
-  } else {
-    for (int n = lane; n < nz; n += 32) {
-      const float2 y = Y[pidx(n)];
-      const float env = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
-      col[n] = env;
-      mx = fmaxf(mx, env);
-    }
-  }
-}
-
-// k_post for 64 <= M <= 1024: two M-point buffers per warp (in-place FFTs).
-// Same algorithm as k_post below: pack two real columns, forward FFT, split
+// ---- k_post_inplace: 64 <= M <= 1024, two M-point buffers per warp ----
+// Same algorithm as k_post below (pack two real columns, forward FFT, split
 // the spectra with the conjugate symmetry, mask, conjugate, forward FFT of
-// each half, modulus / M.
+// each half, modulus / M), arranged so that shared memory is crossed as few
+// times as possible:
+//   * the first radix-8 pass of the forward FFT reads its inputs straight
+//     from the image columns (coalesced across the lanes);
+//   * the spectrum split is fused into the first pass of both inverse
+//     transforms (each input of that pass is formed from Z[n] and Z[M-n]);
+//   * the last pass of each inverse transform writes the envelope straight
+//     to the image.
+// Every pass is a radix-8 Stockham pass except a final radix-4 / radix-2
+// pass when log2 M is not a multiple of 3; the first pass (sub-transform
+// length 1) needs no twiddles.
+
+template <int MPL>
+struct PostShape {
+  static constexpr int M = 32 * MPL;
+  static constexpr int LOG2 = MPL == 2 ? 6 : MPL == 4 ? 7 : MPL == 8 ? 8 : MPL == 16 ? 9 : 10;
+  static constexpr int G1 = M / 8;                      // radix-8 groups of a pass
+  static constexpr int GPL = G1 >= 32 ? G1 / 32 : 1;    // groups per lane
+};
+
+// First forward pass: x[r] = (a[n], b[n]), n = j + r M/8, zero past nz.
+template <int MPL>
+__device__ __forceinline__ void first_pass_from_columns(float2* A, const float* ca, const float* cb,
+                                                        int nz, bool two, int lane) {
+  using S = PostShape<MPL>;
+#pragma unroll
+  for (int t = 0; t < S::GPL; ++t) {
+    const int j = lane + 32 * t;
+    if (j >= S::G1) break;
+    float2 x[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int n = j + r * S::G1;
+      const bool in = n < nz;
+      x[r] = make_float2(in ? ca[n] : 0.f, (in && two) ? cb[n] : 0.f);
+    }
+    dft_regs<8>(x);
+    float2* op = A + pidx(8 * j);  // outputs 8j + r: pidx(8j + r) = pidx(8j) + r
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op[r] = x[r];
+  }
+  __syncwarp();
+}
+
+// Spectrum split fused into the first pass of both inverse transforms.
+// Input n of the transform for column a is (h (Z[n] + conj Z[M-n]) / 2)*
+// written out as below, for column b the same with -i; h = mask[n].  The
+// column-b pass output goes to B at once (B is free); the column-a outputs
+// wait in registers until every lane has read Z, then overwrite it in A.
+template <int MPL>
+__device__ __forceinline__ void split_first_pass(float2* A, float2* B, const float* mk, int lane) {
+  using S = PostShape<MPL>;
+  constexpr int M = S::M;
+  float2 xa[S::GPL][8];
+#pragma unroll
+  for (int t = 0; t < S::GPL; ++t) {
+    const int j = lane + 32 * t;
+    if (j >= S::G1) break;
+    float2 xb[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int n = j + r * S::G1;
+      const float2 zn = A[pidx(n)], zm = A[pidx((M - n) & (M - 1))];
+      const float h = 0.5f * mk[n];
+      xa[t][r] = make_float2(h * (zn.x + zm.x), -h * (zn.y - zm.y));
+      xb[r] = make_float2(h * (zn.y + zm.y), h * (zn.x - zm.x));
+    }
+    dft_regs<8>(xb);
+    float2* op = B + pidx(8 * j);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op[r] = xb[r];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < S::GPL; ++t) {
+    const int j = lane + 32 * t;
+    if (j >= S::G1) break;
+    dft_regs<8>(xa[t]);
+    float2* op = A + pidx(8 * j);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) op[r] = xa[t][r];
+  }
+  __syncwarp();
+}
+
+// Last pass (sub-transform length ns = M / R, so group j has k = j and its
+// outputs land at j + r ns in natural order): modulus / M straight to the
+// column, folded into the column maximum.
+template <int R, int MPL>
+__device__ __forceinline__ void last_pass_to_column(const float2* buf, const float2* twp, float* col,
+                                                    int nz, float inv_m, float& mx, int lane) {
+  constexpr int M = 32 * MPL, ns = M / R, groups = M / R;
+  constexpr int is = groups + (groups >> 3);
+#pragma unroll
+  for (int t = 0; t < (groups + 31) / 32; ++t) {
+    const int j = lane + 32 * t;
+    if (j >= groups) break;
+    float2 x[R];
+    const float2* ip = buf + pidx(j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = ip[r * is];
+    float2 w[R];
+    twiddles<R>(twp, j, w);
+#pragma unroll
+    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
+    dft_regs<R>(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = j + r * ns;
+      const float e = sqrtf(x[r].x * x[r].x + x[r].y * x[r].y) * inv_m;
+      if (n < nz) {
+        col[n] = e;
+        mx = fmaxf(mx, e);
+      }
+    }
+  }
+}
+
+// Passes after the first (twiddle blocks from the second pass on), the last
+// one writing the envelope; to_column = false keeps every pass in shared
+// memory (the forward transform).
+template <int MPL>
+__device__ __forceinline__ void rest_passes(float2* buf, const float2* tw, bool to_column,
+                                            float* col, int nz, float inv_m, float& mx, int lane) {
+  constexpr int M = 32 * MPL;
+  int ns = 8, rem = PostShape<MPL>::LOG2 - 3;
+  const float2* twp = tw;
+  while (rem > 0) {
+    const int lr = rem >= 3 ? 3 : rem;
+    if (to_column && lr == rem) {
+      if (lr == 3) last_pass_to_column<8, MPL>(buf, twp, col, nz, inv_m, mx, lane);
+      else if (lr == 2) last_pass_to_column<4, MPL>(buf, twp, col, nz, inv_m, mx, lane);
+      else last_pass_to_column<2, MPL>(buf, twp, col, nz, inv_m, mx, lane);
+      return;
+    }
+    if (lr == 3) stockham_pass_inplace<8, MPL>(buf, M, ns, twp, lane);
+    else if (lr == 2) stockham_pass_inplace<4, MPL>(buf, M, ns, twp, lane);
+    else stockham_pass_inplace<2, MPL>(buf, M, ns, twp, lane);
+    twp += ns * ((1 << lr) - 1);
+    ns <<= lr;
+    rem -= lr;
+  }
+}
+
 template <int MPL>
 __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   extern __shared__ __align__(16) float2 sbuf[];
@@ -293,50 +387,15 @@ __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
                      (size_t)j0 * p.nz;
   float* dst = p.out + ((size_t)f * p.planes + (size_t)p.s_dst * p.n_out + o) * plane +
                (size_t)j0 * p.nz;
-  const bool vec = (p.nz & 3) == 0;
-  if (vec) {
-    for (int n = 4 * lane; n < M; n += 128) {
-      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-      if (n < p.nz) {
-        a = *reinterpret_cast<const float4*>(src + n);
-        if (two) b = *reinterpret_cast<const float4*>(src + p.nz + n);
-      }
-      A[pidx(n)] = make_float2(a.x, b.x);
-      A[pidx(n + 1)] = make_float2(a.y, b.y);
-      A[pidx(n + 2)] = make_float2(a.z, b.z);
-      A[pidx(n + 3)] = make_float2(a.w, b.w);
-    }
-  } else {
-    for (int n = lane; n < M; n += 32) {
-      const bool in_col = n < p.nz;
-      const float a = in_col ? src[n] : 0.f;
-      const float b = (in_col && two) ? src[p.nz + n] : 0.f;
-      A[pidx(n)] = make_float2(a, b);
-    }
-  }
-  __syncwarp();
-  fft_inplace<MPL>(A, M, p.log2m, tw, lane);
-  for (int k = lane; k <= M / 2; k += 32) {
-    const int km = (M - k) & (M - 1);
-    const float2 z = A[pidx(k)], zc = A[pidx(km)];
-    const float hk = 0.5f * mk[k];
-    B[pidx(k)] = make_float2(hk * (z.x + zc.x), -hk * (z.y - zc.y));
-    A[pidx(k)] = make_float2(hk * (z.y + zc.y), hk * (z.x - zc.x));
-    if (km != k) {
-      const float hm = 0.5f * mk[km];
-      B[pidx(km)] = make_float2(hm * (zc.x + z.x), -hm * (zc.y - z.y));
-      A[pidx(km)] = make_float2(hm * (zc.y + z.y), hm * (zc.x - z.x));
-    }
-  }
-  __syncwarp();
-  const float inv_m = 1.0f / (float)M;
+  // forward transform of a + i b
+  first_pass_from_columns<MPL>(A, src, src + p.nz, p.nz, two, lane);
   float mx = 0.f;
-  fft_inplace<MPL>(B, M, p.log2m, tw, lane);
-  emit_env(B, dst, p.nz, vec, inv_m, lane, mx);
-  if (two) {
-    fft_inplace<MPL>(A, M, p.log2m, tw, lane);
-    emit_env(A, dst + p.nz, p.nz, vec, inv_m, lane, mx);
-  }
+  rest_passes<MPL>(A, tw, false, nullptr, 0, 0.f, mx, lane);
+  // split + masks, first inverse pass of both columns
+  split_first_pass<MPL>(A, B, mk, lane);
+  const float inv_m = 1.0f / (float)M;
+  rest_passes<MPL>(A, tw, true, dst, p.nz, inv_m, mx, lane);
+  if (two) rest_passes<MPL>(B, tw, true, dst + p.nz, p.nz, inv_m, mx, lane);
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
   if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
