@@ -119,6 +119,11 @@ __device__ __forceinline__ void combine(const double* P, float& das, float& dmas
       ho = das;
     } else if constexpr (K == 2) {
       ho = dmas;
+    } else if constexpr (K == 3) {
+      // k = 3 written out (Eq. 7 in power sums): e3 = (p1^3 - 3 p1 p2 + 2 p3) / 6
+      // (p1^2 is exact in FP64, each FMA rounds once)
+      const double t = fma(P[3], P[3], -3.0 * P[4]);
+      ho = (float)(fma(t, P[3], 2.0 * P[0]) * (1.0 / 6.0));
     } else {
       double p[K + 1];
 #pragma unroll

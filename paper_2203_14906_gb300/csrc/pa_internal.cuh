@@ -19,8 +19,13 @@ constexpr int kC = 4;
 // at most kNCMax) and the virtual channels staged per chunk (steps + kC - 1).
 constexpr int kNCMax = 72;
 constexpr int kNCSMax = kNCMax + kC - 1;
-// Channel steps between Kahan folds of the compensated power sums.
-constexpr int kFoldBlocks = 2;  // blocks of kC steps
+// Channel steps between Kahan folds of the compensated power sums: plain
+// FP32 partial sums over 32 channels, compensated across folds.  Measured on
+// GB300 (BF16 RF, 128 channels, k = 3): folding every 8 / 16 / 32 steps takes
+// 0.937 / 0.894 / 0.877 ms per 32-frame launch, and the error against the
+// FP64 oracle on the same (dequantised) RF stays below 5e-7 of the image
+// peak for k = 3..5 at 256 channels.
+constexpr int kFoldBlocks = 8;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
 // Shared-memory layout of the fused kernel: work-item words and the TMA
 // mbarrier (16 B), channel bases and window starts (kCbInts ints each,
