@@ -184,9 +184,11 @@ def sm_max_mhz():
 
 
 def kernel_source_hash():
+    """Hash of the fused kernel's sources and of the plan code that sizes its
+    launches (tiles, chunks, shared memory)."""
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
-        if f.startswith("pa_bf"):
+        if f.startswith("pa_bf") or f in ("pa_internal.cuh", "pa_plan.cu"):
             h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
