@@ -174,6 +174,10 @@ pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
  * return.  Copies overlap with compute across frames.  Pinned (page-locked)
  * host memory gives the full copy rate.  Device staging buffers are
  * allocated on first use and owned by the plan.
+ * Errors: as pa_beamform, plus PA_ETIMEOUT when a thread block of the fused
+ * kernel gave up waiting for its TMA staging copies during this call (a
+ * bounded wait of about a second; the block stops early, so the output is
+ * incomplete; pa_plan_info.device_error_flags has bit 8 set).
  */
 pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
                            int32_t n_frames, float* out_host, uint32_t stages,
@@ -257,7 +261,9 @@ double pa_server_now(pa_server_t srv);
  * (<= now: immediately; later values replay a recorded arrival trace).
  * desc->max_batch is ignored (the server's max_batch applies).
  * Errors: PA_EINVAL (descriptor or pointers), PA_ENOMEM (one frame alone
- * needs more than the budget).  The call never blocks on the device.
+ * needs more than the budget).  The call never blocks on the device.  A
+ * request whose batch hit a timed-out staging wait in the fused kernel
+ * completes with status PA_ETIMEOUT.
  */
 pa_status pa_server_submit(pa_server_t srv, const pa_plan_desc* desc, const void* rf_host,
                            float* out_host, double arrival_s, uint64_t* ticket);

@@ -292,7 +292,7 @@ __device__ __forceinline__ int window_start(const BfParams& p, int tile_id, int 
 // Issue the boxes of chunk k of (tile, frame); every thread calls it.
 __device__ __forceinline__ void tma_issue_chunk(const BfParams& p, int frame, int k, int cv, int lo,
                                                 int* s_lo, uint32_t raw_s, uint32_t mbar) {
-  if (threadIdx.x == 0) mbar_expect(mbar, p.chunk_bytes);
+  if (threadIdx.x == 0) mbar_expect(mbar, p.chunk_bytes + p.expect_extra);
   if (cv >= 0) {
     const int elt = p.rf_dtype == PA_RF_F32 ? 4 : 2;
     s_lo[cv] = lo;
@@ -462,7 +462,10 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         const bool ok = mbar_wait_bounded(mbar, phase);
         phase ^= 1;
         if (!__syncthreads_and(ok)) {
-          if (threadIdx.x == 0) atomicOr(p.err, 8);
+          if (threadIdx.x == 0) {
+            atomicOr(p.err, 8);
+            atomicAdd(p.timeouts, 1);
+          }
           timed_out = true;
           break;
         }

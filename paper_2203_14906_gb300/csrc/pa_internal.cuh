@@ -88,7 +88,10 @@ struct BfParams {  // aligned as CUtensorMap requires
   int n_frames;           // frames in this launch
   int n_items;            // n_tiles * n_frames
   int* counter;           // work counter (zeroed before launch)
-  int* err;               // bounds-check error word (checked builds)
+  int* err;               // error flags: 1, 2 index checks (checked builds), 8 a wait ran out
+  int* timeouts;          // running count of blocks whose bounded TMA wait ran out
+  int expect_extra;       // bytes added to every chunk's expected transaction
+                          // count: 0, or > 0 only to test the bounded wait
 };
 
 // Post-filter / envelope parameters (one warp per depth column).
@@ -152,6 +155,9 @@ PA_DECLARE_ORDER(8)
 
 // Sets the thread-local message returned by pa_last_error().
 void set_error_message(const char* msg);
+// Device address of the plan's running count of timed-out waits (the word
+// pa_beamform's launches update), for the server's completion check.
+int* plan_timeout_counter(pa_plan_s* P);
 
 cudaError_t post_configure(size_t smem);
 cudaError_t post_launch(const PostParams& p, cudaStream_t s);

@@ -67,6 +67,8 @@ struct pa_plan_s {
   bool use_tma = false;
   int lo_align = 4;   // window starts are multiples of this many samples
   int nc = 32;        // channel steps per staged chunk (multiple of kC)
+  int expect_extra = 0;   // > 0 only under PA_INJECT_TMA_SHORTFALL (tests the bounded wait)
+  long long timeouts_seen = 0;  // timed-out waits already reported by pa_beamform_host
   int wr = 0;         // raw samples per channel delivered by one TMA box
   int rp = 0;         // raw-buffer row pitch in samples (128-byte aligned rows)
   int pairs_off = 0;  // shared-memory offset of the interpolation slots
@@ -406,6 +408,10 @@ void configure(pa_plan_s* P) {
   // vectorised loads win for FP32 RF (the FP32 raw buffer costs a resident
   // block per SM).  PA_STAGING=tma|loads overrides the choice.
   P->use_tma = (d.n_samples % P->lo_align) == 0 && P->elt == 2;
+  // Failure injection for tests: every chunk expects 16 bytes more than its
+  // boxes deliver, so each block's bounded wait runs out (about a second),
+  // sets error flag 8, counts a timeout and ends; no copy is left in flight.
+  P->expect_extra = getenv("PA_INJECT_TMA_SHORTFALL") ? 16 : 0;
   const char* staging = getenv("PA_STAGING");
   if (staging && strcmp(staging, "loads") == 0) P->use_tma = false;
   if (staging && strcmp(staging, "tma") == 0) P->use_tma = (d.n_samples % P->lo_align) == 0;
@@ -505,7 +511,9 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   if ((s = dalloc(P, &P->vchunks, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
   if ((s = dalloc(P, &P->tw, (size_t)2 * P->M)) != PA_OK) return s;  // >= n_tw
   if ((s = dalloc(P, &P->mask, (size_t)3 * P->M)) != PA_OK) return s;
-  P->scratch_ints = 2 + (size_t)P->d.max_batch * 3;
+  // [0] error flags, [1] work counter, [2, 2 + 3 max_batch) image maxima,
+  // [last] running count of timed-out waits
+  P->scratch_ints = 3 + (size_t)P->d.max_batch * 3;
   if ((s = dalloc(P, &P->scratch[0], P->scratch_ints)) != PA_OK) return s;
   PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
 
@@ -846,6 +854,8 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.n_items = P->n_tiles * P->ngroups * nf;
   b.counter = scratch + 1;
   b.err = scratch;
+  b.timeouts = scratch + P->scratch_ints - 1;
+  b.expect_extra = P->expect_extra;
   c->sb.func = bf_func(P->K, P->apod, P->comp);
   c->sb.grid = dim3(std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms)));
   c->sb.block = dim3(P->threads);
@@ -987,6 +997,10 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
 // ------------------------------------------------------------ dispatchers
 namespace pa {
 void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
+int* plan_timeout_counter(pa_plan_s* P) {
+  return P && P->scratch[0] ? P->scratch[0] + P->scratch_ints - 1 : nullptr;
+}
 
 cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p, int grid, int block,
                       size_t smem, cudaStream_t s) {
@@ -1187,6 +1201,21 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   }
   PA_CUDA(cudaStreamSynchronize(P->hs[0]));
   PA_CUDA(cudaStreamSynchronize(P->hs[1]));
+  // bounded waits that ran out during this call (the kernel stopped early)
+  if (P->use_tma) {
+    long long total = 0;
+    for (int b = 0; b < 2; ++b) {
+      int n = 0;
+      PA_CUDA(cudaMemcpy(&n, P->scratch[b] + P->scratch_ints - 1, sizeof n, cudaMemcpyDeviceToHost));
+      total += n;
+    }
+    if (total > P->timeouts_seen) {
+      const long long fresh = total - P->timeouts_seen;
+      P->timeouts_seen = total;
+      return fail(PA_ETIMEOUT, "%lld thread block(s) gave up waiting for their RF staging copies",
+                  fresh);
+    }
+  }
   return PA_OK;
 }
 

@@ -51,11 +51,13 @@ struct PlanEntry {
   size_t bytes = 0;
   bool busy = false;
   uint64_t last_used = 0;
+  int timeouts_seen = 0;  // timed-out waits of this plan already charged to a batch
 };
 
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
+  int* h_timeouts = nullptr;  // pinned copy of the plan's timed-out-wait count after the batch
   bool busy = false;
   std::vector<Request*> reqs;
   size_t bytes = 0;
@@ -122,9 +124,14 @@ struct pa_server_s {
       cudaError_t e = cudaEventQuery(s.ev);
       if (e == cudaErrorNotReady) continue;
       const double t = now();
+      pa_status done = e == cudaSuccess ? PA_OK : PA_ECUDA;
+      if (done == PA_OK && *s.h_timeouts > s.pe->timeouts_seen) {
+        s.pe->timeouts_seen = *s.h_timeouts;
+        done = PA_ETIMEOUT;  // the fused kernel gave up waiting for its staging copies
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
-        for (Request* r : s.reqs) finish(r, e == cudaSuccess ? PA_OK : PA_ECUDA, t);
+        for (Request* r : s.reqs) finish(r, done, t);
         in_use -= s.bytes;
       }
       if (e != cudaSuccess) cudaGetLastError();
@@ -232,6 +239,12 @@ struct pa_server_s {
       }
       if (rf_dev) cudaFreeAsync(rf_dev, s.st);
       if (out_dev) cudaFreeAsync(out_dev, s.st);
+      // a bounded wait that ran out inside the batch shows in the plan's count
+      if (e == cudaSuccess && st == PA_OK) {
+        *s.h_timeouts = pe.timeouts_seen;
+        const int* cnt = pa::plan_timeout_counter(pe.plan);
+        if (cnt) e = cudaMemcpyAsync(s.h_timeouts, cnt, sizeof(int), cudaMemcpyDeviceToHost, s.st);
+      }
       if (e == cudaSuccess && st == PA_OK) e = cudaEventRecord(s.ev, s.st);
       const double t = now();
       std::lock_guard<std::mutex> lk(mu);
@@ -332,12 +345,15 @@ pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
   for (auto& s : S->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_timeouts, sizeof(int));
+    if (e == cudaSuccess) *s.h_timeouts = 0;
   }
   if (e != cudaSuccess) {
     pa::set_error_message(cudaGetErrorString(e));
     for (auto& s : S->slots) {
       if (s.st) cudaStreamDestroy(s.st);
       if (s.ev) cudaEventDestroy(s.ev);
+      if (s.h_timeouts) cudaFreeHost(s.h_timeouts);
     }
     if (S->plan_stream) cudaStreamDestroy(S->plan_stream);
     if (S->pool) cudaMemPoolDestroy(S->pool);
@@ -466,6 +482,7 @@ pa_status pa_server_destroy(pa_server_t S) {
     cudaStreamSynchronize(s.st);
     cudaStreamDestroy(s.st);
     cudaEventDestroy(s.ev);
+    cudaFreeHost(s.h_timeouts);
   }
   cudaStreamDestroy(S->plan_stream);
   cudaMemPoolDestroy(S->pool);
