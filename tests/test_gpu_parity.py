@@ -40,6 +40,18 @@ def test_cfg1_every_order(k):
     assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"cfg1 k={k}")
 
 
+@pytest.mark.parametrize("k", [6, 7, 8])
+def test_high_orders_compensated_bf16(k):
+    """Orders 6-8 on the compensated BF16 path (generic roots and powers,
+    Newton's identities in FP64)."""
+    wl = synth.workload("cfg1", rf_dtype="bf16")
+    rf = _frames(wl, [2])
+    out, info, deq = run_gpu(wl, rf, k, rf_dtype="bf16", compensated=1)
+    assert info["device_error_flags"] == 0
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"bf16 k={k} compute")
+    assert_parity(compare(out, oracle_frames(wl, rf, k)), TOL_LP, what=f"bf16 k={k} e2e")
+
+
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_cfg2_full_size(k):
     """cfg2 at full size: 128 el x 2048 samples, 512x512, orders 2..5."""
