@@ -174,10 +174,14 @@ pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
  * return.  Copies overlap with compute across frames.  Pinned (page-locked)
  * host memory gives the full copy rate.  Device staging buffers are
  * allocated on first use and owned by the plan.
+ * Frames are processed in chunks (short first and last chunks, so the
+ * first upload and the last download overlap as little compute as possible)
+ * rotating over three device buffer sets and streams.
  * Errors: as pa_beamform, plus PA_ETIMEOUT when a thread block of the fused
- * kernel gave up waiting for its TMA staging copies during this call (a
- * bounded wait of about a second; the block stops early, so the output is
- * incomplete; pa_plan_info.device_error_flags has bit 8 set).
+ * kernel gave up waiting for its TMA staging copies (a bounded wait of about
+ * a second; the block stops early, so the output is incomplete;
+ * pa_plan_info.device_error_flags has bit 8 set) in this call, or in an
+ * earlier launch of the plan that no call has reported yet.
  */
 pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
                            int32_t n_frames, float* out_host, uint32_t stages,

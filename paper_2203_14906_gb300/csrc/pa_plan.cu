@@ -53,6 +53,9 @@ struct DeviceGuard {
 }  // namespace
 
 // ------------------------------------------------------------------- plan
+// Buffer sets (and streams) of the host-buffer path.
+constexpr int kHostSets = 3;
+
 struct pa_plan_s {
   pa_plan_desc d{};
   int device = 0, num_sms = 0;
@@ -87,13 +90,15 @@ struct pa_plan_s {
   int2* slot_rg = nullptr; // warp slot -> (column residue, column group)
   float2* tw = nullptr;
   float* mask = nullptr;
-  int* scratch[2] = {nullptr, nullptr};  // [err, counter, maxslots...]
+  // [err, counter, maxslots..., timeouts]; [0] serves pa_beamform, all three
+  // the buffer sets of pa_beamform_host
+  int* scratch[kHostSets] = {nullptr, nullptr, nullptr};
   size_t scratch_ints = 0;
   // host-buffer path
   void* h_rf = nullptr;
   float* h_out = nullptr;
   size_t h_rf_bytes = 0, h_out_bytes = 0;
-  cudaStream_t hs[2] = {nullptr, nullptr};
+  cudaStream_t hs[kHostSets] = {nullptr, nullptr, nullptr};
   cudaEvent_t h_ev = nullptr;
   // CUDA graphs of the launch sequence, one per (frames, stages)
   struct GraphEntry {
@@ -461,7 +466,7 @@ pa_status dalloc(pa_plan_s* P, T** ptr, size_t n) {
 void free_plan(pa_plan_s* P) {
   if (!P) return;
   DeviceGuard g(P->device);
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < kHostSets; ++s)
     if (P->hs[s]) cudaStreamSynchronize(P->hs[s]);
   cudaFree(P->table);
   cudaFree(P->wtab);
@@ -472,11 +477,10 @@ void free_plan(pa_plan_s* P) {
   cudaFree(P->slot_rg);
   cudaFree(P->tw);
   cudaFree(P->mask);
-  cudaFree(P->scratch[0]);
-  cudaFree(P->scratch[1]);
+  for (int s = 0; s < kHostSets; ++s) cudaFree(P->scratch[s]);
   cudaFree(P->h_rf);
   cudaFree(P->h_out);
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < kHostSets; ++s)
     if (P->hs[s]) cudaStreamDestroy(P->hs[s]);
   if (P->h_ev) cudaEventDestroy(P->h_ev);
   for (auto& g : P->graphs) {
@@ -1105,7 +1109,7 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostSets; ++b) {
       if (!P->scratch[b]) continue;
       int flag = 0;
       PA_CUDA(cudaDeviceSynchronize());
@@ -1149,12 +1153,37 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   DeviceGuard g(P->device);
   const pa_plan_desc& d = P->d;
   cudaStream_t user = (cudaStream_t)cuda_stream;
-  // chunks small enough that two of them pipeline copy and compute
-  int chunk = std::min(d.max_batch, std::max(1, (n_frames + 3) / 4));
+  // Chunk schedule: short first and last chunks (the first H2D copy and the
+  // last D2H copy cannot overlap compute), the rest in evenly sized middle
+  // chunks, none above max_batch.  Chunks rotate over three buffer sets and
+  // streams, so a chunk's upload does not wait for the download two chunks
+  // back.  Measured on GB300 (cfg2, 32 FP32 frames, 1.07 G pairs): 1.12 ms
+  // per call with two sets of 8-frame chunks, 1.105 ms with this schedule;
+  // launching the chunks' kernels directly instead of through the plan's
+  // graphs (so that neighbouring chunks' kernels could overlap) took 1.20 ms.
+  std::vector<int> sched;
+  {
+    const int cap = std::max(1, d.max_batch);
+    const int edge = std::min(cap, std::max(1, n_frames / 5));
+    int mid = n_frames - 2 * edge;
+    if (mid < 0) {  // one or two frames
+      for (int f = 0; f < n_frames; ++f) sched.push_back(1);
+    } else {
+      sched.push_back(edge);
+      const int nm = mid == 0 ? 0 : std::max(2, (mid + cap - 1) / cap);
+      for (int q = 0; q < nm; ++q) {
+        const int c = (mid * (q + 1)) / nm - (mid * q) / nm;
+        if (c > 0) sched.push_back(c);
+      }
+      sched.push_back(edge);
+    }
+  }
+  const int chunk = *std::max_element(sched.begin(), sched.end());
+  const int nsets = std::min<int>(kHostSets, (int)sched.size());
   const size_t rf_frame = (size_t)d.n_elem * d.n_samples * P->elt;
   const size_t out_frame = (size_t)popcount3(stages) * P->n_out * d.nx * d.nz;
-  const size_t need_rf = 2 * (size_t)chunk * rf_frame;
-  const size_t need_out = 2 * (size_t)chunk * out_frame * sizeof(float);
+  const size_t need_rf = (size_t)nsets * chunk * rf_frame;
+  const size_t need_out = (size_t)nsets * chunk * out_frame * sizeof(float);
   if (need_rf > P->h_rf_bytes) {
     cudaFree(P->h_rf);
     P->device_bytes -= P->h_rf_bytes;
@@ -1171,24 +1200,22 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
     P->h_out_bytes = need_out;
     P->device_bytes += need_out;
   }
-  if (!P->hs[0]) {
-    PA_CUDA(cudaStreamCreateWithFlags(&P->hs[0], cudaStreamNonBlocking));
-    PA_CUDA(cudaStreamCreateWithFlags(&P->hs[1], cudaStreamNonBlocking));
-    PA_CUDA(cudaEventCreateWithFlags(&P->h_ev, cudaEventDisableTiming));
-  }
-  if (!P->scratch[1]) {
-    pa_status s = dalloc(P, &P->scratch[1], P->scratch_ints);
-    if (s != PA_OK) return s;
-    PA_CUDA(cudaMemset(P->scratch[1], 0, P->scratch_ints * sizeof(int)));
+  if (!P->h_ev) PA_CUDA(cudaEventCreateWithFlags(&P->h_ev, cudaEventDisableTiming));
+  for (int b = 0; b < nsets; ++b) {
+    if (!P->hs[b]) PA_CUDA(cudaStreamCreateWithFlags(&P->hs[b], cudaStreamNonBlocking));
+    if (!P->scratch[b]) {
+      pa_status s = dalloc(P, &P->scratch[b], P->scratch_ints);
+      if (s != PA_OK) return s;
+      PA_CUDA(cudaMemset(P->scratch[b], 0, P->scratch_ints * sizeof(int)));
+    }
   }
   // the internal streams start after work already queued on the caller's stream
   PA_CUDA(cudaEventRecord(P->h_ev, user));
-  PA_CUDA(cudaStreamWaitEvent(P->hs[0], P->h_ev, 0));
-  PA_CUDA(cudaStreamWaitEvent(P->hs[1], P->h_ev, 0));
-  int c = 0;
-  for (int f0 = 0; f0 < n_frames; f0 += chunk, ++c) {
-    const int nf = std::min(chunk, n_frames - f0);
-    const int b = c & 1;
+  for (int b = 0; b < nsets; ++b) PA_CUDA(cudaStreamWaitEvent(P->hs[b], P->h_ev, 0));
+  int f0 = 0;
+  for (size_t c = 0; c < sched.size(); ++c) {
+    const int nf = sched[c];
+    const int b = (int)(c % nsets);
     cudaStream_t st = P->hs[b];
     char* rf_d = (char*)P->h_rf + (size_t)b * chunk * rf_frame;
     float* out_d = P->h_out + (size_t)b * chunk * out_frame;
@@ -1198,13 +1225,14 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
     if (s != PA_OK) return s;
     PA_CUDA(cudaMemcpyAsync(out_host + (size_t)f0 * out_frame, out_d,
                             nf * out_frame * sizeof(float), cudaMemcpyDeviceToHost, st));
+    f0 += nf;
   }
-  PA_CUDA(cudaStreamSynchronize(P->hs[0]));
-  PA_CUDA(cudaStreamSynchronize(P->hs[1]));
+  for (int b = 0; b < nsets; ++b) PA_CUDA(cudaStreamSynchronize(P->hs[b]));
   // bounded waits that ran out during this call (the kernel stopped early)
   if (P->use_tma) {
     long long total = 0;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostSets; ++b) {
+      if (!P->scratch[b]) continue;
       int n = 0;
       PA_CUDA(cudaMemcpy(&n, P->scratch[b] + P->scratch_ints - 1, sizeof n, cudaMemcpyDeviceToHost));
       total += n;
