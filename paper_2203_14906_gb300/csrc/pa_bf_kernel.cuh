@@ -352,6 +352,8 @@ __device__ __forceinline__ ItemInfo decode_item(const BfParams& p, int item) {
   return it;
 }
 
+// Kahan fold of the partial sums into the running totals, held in registers
+// (orders <= 3: the plain kernel's register budget is the limit anyway).
 template <int NA>
 __device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC][NA],
                                            float (&cmp)[kC][NA]) {
@@ -368,15 +370,53 @@ __device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC
   }
 }
 
-// Resident 256-thread blocks per SM the register allocation targets: three
-// (80 registers) for plain sums of orders <= 5, two for the larger accumulator
-// sets of compensated sums and orders >= 6.
+// The same fold with totals and compensation terms in shared memory (float4
+// q of thread t holds accumulator q of the thread's kC = 4 columns; the
+// compensation terms follow the NA totals).  Orders >= 4 use it: their larger
+// accumulator sets would otherwise halve the resident blocks, and the sums
+// are touched once per fold only (every kFoldBlocks * kC steps).  Measured on
+// GB300 (cfg5, k = 4, BF16, apodised): 4.71 -> 4.36 ms per 64-frame launch;
+// at k = 3 (cfg2) the register form is faster (0.877 vs 0.977 ms).
+template <int NA>
+__device__ __forceinline__ void kahan_fold_shared(float (&acc)[kC][NA], float4* s_sum) {
+  static_assert(kC == 4, "one float4 per accumulator");
+  const int bd = blockDim.x, t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    float4 tv = s_sum[q * bd + t], cv = s_sum[(NA + q) * bd + t];
+    float* tt = reinterpret_cast<float*>(&tv);
+    float* cc = reinterpret_cast<float*>(&cv);
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      const float y = acc[c][q] - cc[c];
+      const float s = tt[c] + y;
+      cc[c] = (s - tt[c]) - y;
+      tt[c] = s;
+      acc[c][q] = 0.f;
+    }
+    s_sum[q * bd + t] = tv;
+    s_sum[(NA + q) * bd + t] = cv;
+  }
+}
+
+// Compensated sums of order K keep their totals in shared memory.
+template <int K, bool COMP>
+struct SharedSums {
+  static constexpr bool value = COMP && K >= 4;
+};
+
+// Resident 256-thread blocks per SM the register allocation targets: four
+// (64 registers) for plain orders <= 3, three (80 registers) for orders 4-5
+// (compensated ones with their totals in shared memory), two for compensated
+// orders <= 3 (totals in registers) and for orders >= 6.
 #ifndef PA_MINB4_MAX_K
 #define PA_MINB4_MAX_K 3
 #endif
 template <int K, bool COMP>
 struct MinBlocks {
-  static constexpr int value = (COMP || K >= 6) ? 2 : (K <= PA_MINB4_MAX_K ? 4 : 3);
+  static constexpr int value = (K >= 6 || (COMP && !SharedSums<K, COMP>::value))
+                                   ? 2
+                                   : (K <= PA_MINB4_MAX_K ? 4 : 3);
 };
 
 template <int K, bool APOD, bool COMP>
@@ -426,13 +466,19 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     const int2 vk = __ldg(p.vchunks + (size_t)tile_id * p.ngroups + grp);
 
     float acc[kC][NA];
-    float tot[COMP ? kC : 1][COMP ? NA : 1];
-    float cmp[COMP ? kC : 1][COMP ? NA : 1];
+    constexpr bool SSUM = SharedSums<K, COMP>::value;
+    float tot[COMP && !SSUM ? kC : 1][COMP && !SSUM ? NA : 1];
+    float cmp[COMP && !SSUM ? kC : 1][COMP && !SSUM ? NA : 1];
+    float4* s_sum = reinterpret_cast<float4*>(smem + p.cmp_off);  // SSUM: compensated totals
 #pragma unroll
     for (int c = 0; c < kC; ++c)
 #pragma unroll
       for (int q = 0; q < NA; ++q) acc[c][q] = 0.f;
-    if constexpr (COMP) {
+    if constexpr (SSUM) {
+#pragma unroll
+      for (int q = 0; q < 2 * NA; ++q)
+        s_sum[q * blockDim.x + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if constexpr (COMP) {
 #pragma unroll
       for (int c = 0; c < kC; ++c)
 #pragma unroll
@@ -562,7 +608,8 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         }
         if constexpr (COMP) {
           if (++fold == kFoldBlocks) {
-            kahan_fold<NA>(acc, tot, cmp);
+            if constexpr (SSUM) kahan_fold_shared<NA>(acc, s_sum);
+            else kahan_fold<NA>(acc, tot, cmp);
             fold = 0;
           }
         }
@@ -584,7 +631,8 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       }
     }
     if (timed_out) break;
-    if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);
+    if constexpr (SSUM) kahan_fold_shared<NA>(acc, s_sum);
+    else if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);
     if (threadIdx.x == 0 && (!p.use_tma || vk.x >= vk.y)) {
       s_item[0] = s_item[2];
       s_item[1] = 0;
@@ -600,8 +648,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         double P[NA];
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
-          if constexpr (COMP) {
+          if constexpr (COMP && !SSUM) {
             P[q] = (double)tot[c][q] - (double)cmp[c][q];
+          } else if constexpr (SSUM) {
+            const float4 tv = s_sum[q * blockDim.x + threadIdx.x];
+            const float4 cv = s_sum[(NA + q) * blockDim.x + threadIdx.x];
+            P[q] = (double)reinterpret_cast<const float*>(&tv)[c] -
+                   (double)reinterpret_cast<const float*>(&cv)[c];
           } else {
             P[q] = (double)acc[c][q];
           }

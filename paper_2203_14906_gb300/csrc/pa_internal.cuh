@@ -58,6 +58,7 @@ struct BfParams {  // aligned as CUtensorMap requires
   int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
   int nearest;            // 1: nearest-sample delays (a = 0), one tap per pair
   int nc, ncs;            // channel steps per chunk, virtual channels staged per chunk
+  int cmp_off;            // shared offset of the compensated totals (compensated sums)
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
   const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}

@@ -70,6 +70,7 @@ struct pa_plan_s {
   bool use_tma = false;
   int lo_align = 4;   // window starts are multiples of this many samples
   int nc = 32;        // channel steps per staged chunk (multiple of kC)
+  int cmp_off = 0;    // shared offset of the compensated totals
   int expect_extra = 0;   // > 0 only under PA_INJECT_TMA_SHORTFALL (tests the bounded wait)
   long long timeouts_seen = 0;  // timed-out waits already reported by pa_beamform_host
   int wr = 0;         // raw samples per channel delivered by one TMA box
@@ -423,6 +424,14 @@ void configure(pa_plan_s* P) {
   if (P->d.max_batch <= 0) P->d.max_batch = 1;
 }
 
+// Shared memory of the compensated sums of orders >= 4: a total and a
+// compensation term (float4 over the kC columns) per accumulator per thread.
+size_t sum_bytes(const pa_plan_s* P) {
+  if (!P->comp || P->K < 4) return 0;
+  const int na = P->K <= 2 ? 3 : P->K + 2;
+  return (size_t)2 * na * P->threads * 16;
+}
+
 size_t table_bytes(const pa_plan_s* P) {
   const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
   size_t b = tab_n * sizeof(int2);
@@ -616,7 +625,8 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
     auto smem_for = [&](int c) {
       const int ncs = c + kC - 1;
       const size_t raw = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
-      return (size_t)kRawOff + ((raw + 127) & ~size_t(127)) + (size_t)ncs * P->window * 8;
+      return (size_t)kRawOff + ((raw + 127) & ~size_t(127)) + (size_t)ncs * P->window * 8 +
+             sum_bytes(P);
     };
     auto fits = [&](int c) {
       const int ncs = c + kC - 1;
@@ -689,7 +699,8 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   const int ncs = P->nc + kC - 1;
   const size_t raw_bytes = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
   P->pairs_off = kRawOff + (int)((raw_bytes + 127) & ~size_t(127));
-  P->smem = (size_t)P->pairs_off + (size_t)ncs * P->window * sizeof(float2);
+  P->cmp_off = (int)((size_t)P->pairs_off + (size_t)ncs * P->window * sizeof(float2));  // 16-aligned
+  P->smem = (size_t)P->cmp_off + sum_bytes(P);
   const long long w4 = P->window / 4;
   if ((long long)ncs * w4 * w4 >= (1ll << 20))
     return fail(PA_EUNSUPPORTED, "RF window of %d samples per channel is too wide; use a finer "
@@ -813,6 +824,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.rp = P->rp;
   b.nc = P->nc;
   b.ncs = P->nc + kC - 1;
+  b.cmp_off = P->cmp_off;
   b.chunk_bytes = b.ncs * P->wr * (int)P->elt;
   b.pairs_off = P->pairs_off;
   if (P->use_tma && !encode_rf_map(P, rf, nf, &b.tmap))
