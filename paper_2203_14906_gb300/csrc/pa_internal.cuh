@@ -128,7 +128,8 @@ struct LaunchSpec {
 
 const void* bf_func(int order, bool apod, bool comp);
 void post_spec(const PostParams& p, LaunchSpec* s);
-int post_buffers(int m);  // M-point complex buffers per warp of the post kernel
+int post_buffers(int m);     // M-point complex buffers per team of the post kernel
+int post_team_warps(int m);  // warps per team (column pair) of the post kernel
 void log_spec(const LogParams& p, int num_sms, LaunchSpec* s);
 
 // Launchers (one translation unit per order keeps the builds parallel).

@@ -383,17 +383,18 @@ void configure(pa_plan_s* P) {
     P->M <<= 1;
     ++P->log2M;
   }
-  // twiddles + three M-point complex buffers per warp (two columns per warp)
   // warps per post block: most resident warps per SM for the shared memory
-  // each needs (post_buffers padded M-point buffers per warp + the twiddles)
+  // they need (post_buffers padded M-point buffers per team of
+  // post_team_warps warps, plus the twiddles and mask), in whole teams
   {
-    const size_t per_warp = (size_t)post_buffers(P->M) * (P->M + P->M / 8) * sizeof(float2);
+    const int tw_warps = post_team_warps(P->M);
+    const size_t per_team = (size_t)post_buffers(P->M) * (P->M + P->M / 8) * sizeof(float2);
     const size_t tw = (size_t)P->M * (sizeof(float2) + sizeof(float));  // twiddles + mask
     const size_t sm_bytes = 227 * 1024;
-    int best = 1;
+    int best = tw_warps;
     size_t best_warps = 0;
-    for (int w = 1; w <= 8; ++w) {
-      const size_t blk = w * per_warp + tw + 1024;
+    for (int w = tw_warps; w <= 8; w += tw_warps) {
+      const size_t blk = (w / tw_warps) * per_team + tw + 1024;
       const size_t warps = (sm_bytes / blk) * w;
       if (blk <= 200 * 1024 && warps > best_warps) {
         best_warps = warps;

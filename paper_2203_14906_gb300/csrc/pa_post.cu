@@ -166,20 +166,38 @@ __device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, c
   return in;
 }
 
-// In-place Stockham pass: each lane first reads the R inputs of all its
-// groups into registers, the warp synchronises, then the outputs overwrite
-// the same buffer.  MPL = M / 32 complex values per lane (64 <= M <= 1024).
-template <int R, int MPL>
+// A team of TW warps (TW = 1 or 2) transforms one packed column pair;
+// tl = lane index within the team (0 .. 32 TW - 1).  Teams of two halve the
+// registers and shared memory per warp, so twice as many warps fit an SM.
+struct Team {
+  int tl;  // lane within the team
+  int id;  // team index within the block (named barrier 1 + id for TW = 2)
+};
+
+template <int TW>
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  if constexpr (TW == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + tm.id), "r"(32 * TW) : "memory");
+  }
+}
+
+// In-place Stockham pass: each team lane first reads the R inputs of all its
+// groups into registers, the team synchronises, then the outputs overwrite
+// the same buffer.  M = 32 MPL points (64 <= M <= 1024).
+template <int R, int MPL, int TW>
 __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns, const float2* twp,
-                                                      int lane) {
-  constexpr int GPL = MPL >= R ? MPL / R : 1;  // groups per lane
+                                                      const Team& tm) {
+  constexpr int TL = 32 * TW;
+  constexpr int GPL = (32 * MPL / R) >= TL ? (32 * MPL / R) / TL : 1;  // groups per team lane
   const int groups = m / R;
   const int is = groups + (groups >> 3), os = ns + (ns >> 3);
   const bool strided = (groups & 7) == 0 && (ns == 1 || (ns & 7) == 0);
   float2 x[GPL][R];
 #pragma unroll
   for (int t = 0; t < GPL; ++t) {
-    const int j = lane + 32 * t;
+    const int j = tm.tl + TL * t;
     if (j < groups) {
       if (strided) {
         const float2* ip = buf + pidx(j);
@@ -191,10 +209,10 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
       }
     }
   }
-  __syncwarp();
+  team_sync<TW>(tm);
 #pragma unroll
   for (int t = 0; t < GPL; ++t) {
-    const int j = lane + 32 * t;
+    const int j = tm.tl + TL * t;
     if (j < groups) {
       const int k = j & (ns - 1);
       if (ns > 1) {
@@ -215,10 +233,10 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
       }
     }
   }
-  __syncwarp();
+  team_sync<TW>(tm);
 }
 
-// ---- k_post_inplace: 64 <= M <= 1024, two M-point buffers per warp ----
+// ---- k_post_inplace: 64 <= M <= 1024, two M-point buffers per team ----
 // Same algorithm as k_post below (pack two real columns, forward FFT, split
 // the spectra with the conjugate symmetry, mask, conjugate, forward FFT of
 // each half, modulus / M), arranged so that shared memory is crossed as few
@@ -233,22 +251,23 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
 // pass when log2 M is not a multiple of 3; the first pass (sub-transform
 // length 1) needs no twiddles.
 
-template <int MPL>
+template <int MPL, int TW>
 struct PostShape {
   static constexpr int M = 32 * MPL;
   static constexpr int LOG2 = MPL == 2 ? 6 : MPL == 4 ? 7 : MPL == 8 ? 8 : MPL == 16 ? 9 : 10;
+  static constexpr int TL = 32 * TW;                    // team lanes
   static constexpr int G1 = M / 8;                      // radix-8 groups of a pass
-  static constexpr int GPL = G1 >= 32 ? G1 / 32 : 1;    // groups per lane
+  static constexpr int GPL = G1 >= TL ? G1 / TL : 1;    // groups per team lane
 };
 
 // First forward pass: x[r] = (a[n], b[n]), n = j + r M/8, zero past nz.
-template <int MPL>
+template <int MPL, int TW>
 __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* ca, const float* cb,
-                                                        int nz, bool two, int lane) {
-  using S = PostShape<MPL>;
+                                                        int nz, bool two, const Team& tm) {
+  using S = PostShape<MPL, TW>;
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
-    const int j = lane + 32 * t;
+    const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
     float2 x[8];
 #pragma unroll
@@ -262,7 +281,7 @@ __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* 
 #pragma unroll
     for (int r = 0; r < 8; ++r) op[r] = x[r];
   }
-  __syncwarp();
+  team_sync<TW>(tm);
 }
 
 // Spectrum split fused into the first pass of both inverse transforms.
@@ -270,14 +289,15 @@ __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* 
 // written out as below, for column b the same with -i; h = mask[n].  The
 // column-b pass output goes to B at once (B is free); the column-a outputs
 // wait in registers until every lane has read Z, then overwrite it in A.
-template <int MPL>
-__device__ __forceinline__ void split_first_pass(float2* A, float2* B, const float* mk, int lane) {
-  using S = PostShape<MPL>;
+template <int MPL, int TW>
+__device__ __forceinline__ void split_first_pass(float2* A, float2* B, const float* mk,
+                                                 const Team& tm) {
+  using S = PostShape<MPL, TW>;
   constexpr int M = S::M;
   float2 xa[S::GPL][8];
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
-    const int j = lane + 32 * t;
+    const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
     float2 xb[8];
 #pragma unroll
@@ -293,30 +313,30 @@ __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const flo
 #pragma unroll
     for (int r = 0; r < 8; ++r) op[r] = xb[r];
   }
-  __syncwarp();
+  team_sync<TW>(tm);
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
-    const int j = lane + 32 * t;
+    const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
     dft_regs<8>(xa[t]);
     float2* op = A + pidx(8 * j);
 #pragma unroll
     for (int r = 0; r < 8; ++r) op[r] = xa[t][r];
   }
-  __syncwarp();
+  team_sync<TW>(tm);
 }
 
 // Last pass (sub-transform length ns = M / R, so group j has k = j and its
 // outputs land at j + r ns in natural order): modulus / M straight to the
 // column, folded into the column maximum.
-template <int R, int MPL>
+template <int R, int MPL, int TW>
 __device__ __forceinline__ void last_pass_to_column(const float2* buf, const float2* twp, float* col,
-                                                    int nz, float inv_m, float& mx, int lane) {
-  constexpr int M = 32 * MPL, ns = M / R, groups = M / R;
+                                                    int nz, float inv_m, float& mx, const Team& tm) {
+  constexpr int M = 32 * MPL, ns = M / R, groups = M / R, TL = 32 * TW;
   constexpr int is = groups + (groups >> 3);
 #pragma unroll
-  for (int t = 0; t < (groups + 31) / 32; ++t) {
-    const int j = lane + 32 * t;
+  for (int t = 0; t < (groups + TL - 1) / TL; ++t) {
+    const int j = tm.tl + TL * t;
     if (j >= groups) break;
     float2 x[R];
     const float2* ip = buf + pidx(j);
@@ -342,30 +362,31 @@ __device__ __forceinline__ void last_pass_to_column(const float2* buf, const flo
 // Passes after the first (twiddle blocks from the second pass on), the last
 // one writing the envelope; to_column = false keeps every pass in shared
 // memory (the forward transform).
-template <int MPL>
+template <int MPL, int TW>
 __device__ __forceinline__ void rest_passes(float2* buf, const float2* tw, bool to_column,
-                                            float* col, int nz, float inv_m, float& mx, int lane) {
+                                            float* col, int nz, float inv_m, float& mx,
+                                            const Team& tm) {
   constexpr int M = 32 * MPL;
-  int ns = 8, rem = PostShape<MPL>::LOG2 - 3;
+  int ns = 8, rem = PostShape<MPL, TW>::LOG2 - 3;
   const float2* twp = tw;
   while (rem > 0) {
     const int lr = rem >= 3 ? 3 : rem;
     if (to_column && lr == rem) {
-      if (lr == 3) last_pass_to_column<8, MPL>(buf, twp, col, nz, inv_m, mx, lane);
-      else if (lr == 2) last_pass_to_column<4, MPL>(buf, twp, col, nz, inv_m, mx, lane);
-      else last_pass_to_column<2, MPL>(buf, twp, col, nz, inv_m, mx, lane);
+      if (lr == 3) last_pass_to_column<8, MPL, TW>(buf, twp, col, nz, inv_m, mx, tm);
+      else if (lr == 2) last_pass_to_column<4, MPL, TW>(buf, twp, col, nz, inv_m, mx, tm);
+      else last_pass_to_column<2, MPL, TW>(buf, twp, col, nz, inv_m, mx, tm);
       return;
     }
-    if (lr == 3) stockham_pass_inplace<8, MPL>(buf, M, ns, twp, lane);
-    else if (lr == 2) stockham_pass_inplace<4, MPL>(buf, M, ns, twp, lane);
-    else stockham_pass_inplace<2, MPL>(buf, M, ns, twp, lane);
+    if (lr == 3) stockham_pass_inplace<8, MPL, TW>(buf, M, ns, twp, tm);
+    else if (lr == 2) stockham_pass_inplace<4, MPL, TW>(buf, M, ns, twp, tm);
+    else stockham_pass_inplace<2, MPL, TW>(buf, M, ns, twp, tm);
     twp += ns * ((1 << lr) - 1);
     ns <<= lr;
     rem -= lr;
   }
 }
 
-template <int MPL>
+template <int MPL, int TW>
 __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   extern __shared__ __align__(16) float2 sbuf[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -376,11 +397,13 @@ __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   for (int k = threadIdx.x; k < p.n_tw; k += blockDim.x) tw[k] = __ldg(p.tw + k);
   for (int k = threadIdx.x; k < M; k += blockDim.x) mk[k] = __ldg(p.mask + (size_t)blockIdx.y * M + k);
   __syncthreads();
-  const int j0 = 2 * (blockIdx.x * p.warps_per_block + warp);
+  const Team tm{(warp % TW) * 32 + lane, warp / TW};
+  const int teams = p.warps_per_block / TW;
+  const int j0 = 2 * (blockIdx.x * teams + tm.id);
   const int o = blockIdx.y, f = blockIdx.z;
-  if (j0 >= p.nx) return;  // no block barrier below
+  if (j0 >= p.nx) return;  // the whole team leaves; no block barrier below
   const bool two = j0 + 1 < p.nx;
-  float2* A = sbuf + p.n_tw + M / 2 + (size_t)warp * 2 * MP;
+  float2* A = sbuf + p.n_tw + M / 2 + (size_t)tm.id * 2 * MP;
   float2* B = A + MP;
   const size_t plane = (size_t)p.nx * p.nz;
   const float* src = p.out + ((size_t)f * p.planes + (size_t)p.s_src * p.n_out + o) * plane +
@@ -388,14 +411,14 @@ __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   float* dst = p.out + ((size_t)f * p.planes + (size_t)p.s_dst * p.n_out + o) * plane +
                (size_t)j0 * p.nz;
   // forward transform of a + i b
-  first_pass_from_columns<MPL>(A, src, src + p.nz, p.nz, two, lane);
+  first_pass_from_columns<MPL, TW>(A, src, src + p.nz, p.nz, two, tm);
   float mx = 0.f;
-  rest_passes<MPL>(A, tw, false, nullptr, 0, 0.f, mx, lane);
+  rest_passes<MPL, TW>(A, tw, false, nullptr, 0, 0.f, mx, tm);
   // split + masks, first inverse pass of both columns
-  split_first_pass<MPL>(A, B, mk, lane);
+  split_first_pass<MPL, TW>(A, B, mk, tm);
   const float inv_m = 1.0f / (float)M;
-  rest_passes<MPL>(A, tw, true, dst, p.nz, inv_m, mx, lane);
-  if (two) rest_passes<MPL>(B, tw, true, dst + p.nz, p.nz, inv_m, mx, lane);
+  rest_passes<MPL, TW>(A, tw, true, dst, p.nz, inv_m, mx, tm);
+  if (two) rest_passes<MPL, TW>(B, tw, true, dst + p.nz, p.nz, inv_m, mx, tm);
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
   if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
@@ -545,25 +568,33 @@ cudaError_t post_configure(size_t smem) {
 
 const void* post_inplace_func(int m) {
   switch (m) {
-    case 64: return reinterpret_cast<const void*>(k_post_inplace<2>);
-    case 128: return reinterpret_cast<const void*>(k_post_inplace<4>);
-    case 256: return reinterpret_cast<const void*>(k_post_inplace<8>);
-    case 512: return reinterpret_cast<const void*>(k_post_inplace<16>);
-    case 1024: return reinterpret_cast<const void*>(k_post_inplace<32>);
+    case 64: return reinterpret_cast<const void*>(k_post_inplace<2, 1>);
+    case 128: return reinterpret_cast<const void*>(k_post_inplace<4, 1>);
+    case 256: return reinterpret_cast<const void*>(k_post_inplace<8, 2>);
+    case 512: return reinterpret_cast<const void*>(k_post_inplace<16, 2>);
+    case 1024: return reinterpret_cast<const void*>(k_post_inplace<32, 2>);
   }
   return nullptr;
 }
 
 int post_buffers(int m) { return post_inplace_func(m) ? 2 : 3; }
 
+// Warps per team (one packed column pair): two for the in-place kernel from
+// 256 points on, one for smaller transforms and for the fallback kernel.
+int post_team_warps(int m) { return (post_inplace_func(m) && m >= 256) ? 2 : 1; }
+
 void post_spec(const PostParams& p, LaunchSpec* ls) {
   const size_t mp = (size_t)p.m + (p.m >> 3);
   const void* f = post_inplace_func(p.m);
   ls->func = f ? f : reinterpret_cast<const void*>(k_post);
-  ls->smem = ((size_t)p.warps_per_block * post_buffers(p.m) * mp + p.n_tw) * sizeof(float2) +
+  // in place: two buffers per team of post_team_warps warps; fallback: three
+  // buffers per warp
+  const int tw_warps = post_team_warps(p.m);
+  const int teams = p.warps_per_block / tw_warps;
+  ls->smem = ((size_t)teams * post_buffers(p.m) * mp + p.n_tw) * sizeof(float2) +
              (f ? (size_t)p.m * sizeof(float) : 0);
   const int col_pairs = (p.nx + 1) / 2;
-  ls->grid = dim3((col_pairs + p.warps_per_block - 1) / p.warps_per_block, p.n_out, p.n_frames);
+  ls->grid = dim3((col_pairs + teams - 1) / teams, p.n_out, p.n_frames);
   ls->block = dim3(p.warps_per_block * 32);
 }
 
