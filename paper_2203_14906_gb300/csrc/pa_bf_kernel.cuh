@@ -107,7 +107,8 @@ __device__ __forceinline__ void pair_update(float* v, float s) {
   }
 }
 
-// Newton's identities in FP64: m e_m = sum_{i=1}^m (-1)^(i-1) e_{m-i} p_i.
+// e_k from the power sums in FP64: k = 3, 4, 5 written out (Eqs. 7-9 in power
+// sums), other orders by Newton's identities m e_m = sum_{i=1}^m (-1)^(i-1) e_{m-i} p_i.
 template <int K>
 __device__ __forceinline__ void combine(const double* P, float& das, float& dmas,
                                         float& ho) {
@@ -124,6 +125,25 @@ __device__ __forceinline__ void combine(const double* P, float& das, float& dmas
       // (p1^2 is exact in FP64, each FMA rounds once)
       const double t = fma(P[3], P[3], -3.0 * P[4]);
       ho = (float)(fma(t, P[3], 2.0 * P[0]) * (1.0 / 6.0));
+    } else if constexpr (K == 4) {
+      // Eq. 8 in power sums (p4 = sum |s| for even k):
+      // e4 = (p1^4 - 6 p1^2 p2 + 3 p2^2 + 8 p1 p3 - 6 p4) / 24
+      const double p1 = P[3], p2 = P[4], p3 = P[5], p4 = P[2];
+      const double t = p1 * p1;
+      double e = fma(-6.0, p2, t) * t;
+      e = fma(8.0 * p1, p3, e);
+      e = fma(3.0 * p2, p2, e);
+      ho = (float)(fma(-6.0, p4, e) * (1.0 / 24.0));
+    } else if constexpr (K == 5) {
+      // Eq. 9 in power sums (p5 = sum s for odd k):
+      // e5 = (p1 (p1^4 - 10 p1^2 p2 + 15 p2^2 - 30 p4) + 20 p3 (p1^2 - p2) + 24 p5) / 120
+      const double p1 = P[3], p2 = P[4], p3 = P[5], p4 = P[6], p5 = P[0];
+      const double t = p1 * p1;
+      double e = fma(-10.0, p2, t) * t;
+      e = fma(15.0 * p2, p2, e);
+      e = fma(-30.0, p4, e) * p1;
+      e = fma(20.0 * p3, t - p2, e);
+      ho = (float)(fma(24.0, p5, e) * (1.0 / 120.0));
     } else {
       double p[K + 1];
 #pragma unroll
