@@ -107,62 +107,68 @@ __device__ __forceinline__ void pair_update(float* v, float s) {
   }
 }
 
-// e_k from the power sums in FP64: k = 3, 4, 5 written out (Eqs. 7-9 in power
-// sums), other orders by Newton's identities m e_m = sum_{i=1}^m (-1)^(i-1) e_{m-i} p_i.
+// Outputs of one pixel from its FP32 sums V: V[0] DAS, V[1] sum sgn sqrt|s|,
+// V[2] sum |s|, V[3..] the power sums p1.. of the k-th roots.
+//   DAS as is; DMAS (Eq. 3) in FP32 with an error-free square (q1^2 = h + l
+//   exactly, so (q1^2 - q2) / 2 is rounded about once, as an FP64 evaluation
+//   rounded to FP32 would be); e_k in FP64 from the power sums: k = 3, 4, 5
+//   written out (Eqs. 7-9 in power sums), other orders by Newton's identities
+//   m e_m = sum_{i=1}^m (-1)^(i-1) e_{m-i} p_i.  FP64 is used for e_k only:
+//   on GB300 its rate is a small fraction of FP32, and for small apertures
+//   (apodised images) the epilogue dominates the kernel.
 template <int K>
-__device__ __forceinline__ void combine(const double* P, float& das, float& dmas,
-                                        float& ho) {
-  das = (float)P[0];
+__device__ __forceinline__ void combine(const float* V, float& das, float& dmas, float& ho) {
+  das = V[0];
   {
-    const double dm = 0.5 * fma(P[1], P[1], -P[2]);  // Eq. 3
-    dmas = (float)dm;
-    if constexpr (K == 1) {
-      ho = das;
-    } else if constexpr (K == 2) {
-      ho = dmas;
-    } else if constexpr (K == 3) {
-      // k = 3 written out (Eq. 7 in power sums): e3 = (p1^3 - 3 p1 p2 + 2 p3) / 6
-      // (p1^2 is exact in FP64, each FMA rounds once)
-      const double t = fma(P[3], P[3], -3.0 * P[4]);
-      ho = (float)(fma(t, P[3], 2.0 * P[0]) * (1.0 / 6.0));
-    } else if constexpr (K == 4) {
-      // Eq. 8 in power sums (p4 = sum |s| for even k):
-      // e4 = (p1^4 - 6 p1^2 p2 + 3 p2^2 + 8 p1 p3 - 6 p4) / 24
-      const double p1 = P[3], p2 = P[4], p3 = P[5], p4 = P[2];
-      const double t = p1 * p1;
-      double e = fma(-6.0, p2, t) * t;
-      e = fma(8.0 * p1, p3, e);
-      e = fma(3.0 * p2, p2, e);
-      ho = (float)(fma(-6.0, p4, e) * (1.0 / 24.0));
-    } else if constexpr (K == 5) {
-      // Eq. 9 in power sums (p5 = sum s for odd k):
-      // e5 = (p1 (p1^4 - 10 p1^2 p2 + 15 p2^2 - 30 p4) + 20 p3 (p1^2 - p2) + 24 p5) / 120
-      const double p1 = P[3], p2 = P[4], p3 = P[5], p4 = P[6], p5 = P[0];
-      const double t = p1 * p1;
-      double e = fma(-10.0, p2, t) * t;
-      e = fma(15.0 * p2, p2, e);
-      e = fma(-30.0, p4, e) * p1;
-      e = fma(20.0 * p3, t - p2, e);
-      ho = (float)(fma(24.0, p5, e) * (1.0 / 120.0));
-    } else {
-      double p[K + 1];
+    const float h = V[1] * V[1];
+    const float l = fmaf(V[1], V[1], -h);
+    dmas = 0.5f * ((h - V[2]) + l);
+  }
+  if constexpr (K == 1) {
+    ho = das;
+  } else if constexpr (K == 2) {
+    ho = dmas;
+  } else if constexpr (K == 3) {
+    // e3 = (p1^3 - 3 p1 p2 + 2 p3) / 6 (p1^2 is exact in FP64, each FMA rounds once)
+    const double p1 = V[3], p2 = V[4], p3 = V[0];
+    const double t = fma(p1, p1, -3.0 * p2);
+    ho = (float)(fma(t, p1, 2.0 * p3) * (1.0 / 6.0));
+  } else if constexpr (K == 4) {
+    // e4 = (p1^4 - 6 p1^2 p2 + 3 p2^2 + 8 p1 p3 - 6 p4) / 24, p4 = sum |s| (even k)
+    const double p1 = V[3], p2 = V[4], p3 = V[5], p4 = V[2];
+    const double t = p1 * p1;
+    double e = fma(-6.0, p2, t) * t;
+    e = fma(8.0 * p1, p3, e);
+    e = fma(3.0 * p2, p2, e);
+    ho = (float)(fma(-6.0, p4, e) * (1.0 / 24.0));
+  } else if constexpr (K == 5) {
+    // e5 = (p1 (p1^4 - 10 p1^2 p2 + 15 p2^2 - 30 p4) + 20 p3 (p1^2 - p2) + 24 p5) / 120,
+    // p5 = sum s (odd k)
+    const double p1 = V[3], p2 = V[4], p3 = V[5], p4 = V[6], p5 = V[0];
+    const double t = p1 * p1;
+    double e = fma(-10.0, p2, t) * t;
+    e = fma(15.0 * p2, p2, e);
+    e = fma(-30.0, p4, e) * p1;
+    e = fma(20.0 * p3, t - p2, e);
+    ho = (float)(fma(24.0, p5, e) * (1.0 / 120.0));
+  } else {
+    double p[K + 1];
 #pragma unroll
-      for (int mm = 1; mm < K; ++mm) p[mm] = P[2 + mm];
-      p[K] = (K & 1) ? P[0] : P[2];
-      double e[K + 1];
-      e[0] = 1.0;
+    for (int mm = 1; mm < K; ++mm) p[mm] = V[2 + mm];
+    p[K] = (K & 1) ? V[0] : V[2];
+    double e[K + 1];
+    e[0] = 1.0;
 #pragma unroll
-      for (int mm = 1; mm <= K; ++mm) {
-        double acc = e[mm - 1] * p[1];
+    for (int mm = 1; mm <= K; ++mm) {
+      double acc = e[mm - 1] * p[1];
 #pragma unroll
-        for (int i = 2; i <= mm; ++i) {
-          const double t = e[mm - i] * p[i];
-          acc = (i & 1) ? acc + t : acc - t;
-        }
-        e[mm] = acc * (1.0 / mm);
+      for (int i = 2; i <= mm; ++i) {
+        const double t = e[mm - i] * p[i];
+        acc = (i & 1) ? acc + t : acc - t;
       }
-      ho = (float)e[K];
+      e[mm] = acc * (1.0 / mm);
     }
+    ho = (float)e[K];
   }
 }
 
@@ -658,29 +664,29 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       s_item[1] = 0;
     }
 
-    // ---- FP64 Newton epilogue and store ---------------------------------
+    // ---- epilogue (FP64 e_k) and store -----------------------------------
     const size_t plane = (size_t)p.nx * p.nz;
     const size_t fbase = (size_t)frame * p.planes * plane;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
       const int j = jt + p.m * c;
       if (j < p.nx && z < p.nz) {
-        double P[NA];
+        // compensated sums: total minus compensation, rounded once to FP32
+        float V[NA];
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
           if constexpr (COMP && !SSUM) {
-            P[q] = (double)tot[c][q] - (double)cmp[c][q];
+            V[q] = tot[c][q] - cmp[c][q];
           } else if constexpr (SSUM) {
             const float4 tv = s_sum[q * blockDim.x + threadIdx.x];
             const float4 cv = s_sum[(NA + q) * blockDim.x + threadIdx.x];
-            P[q] = (double)reinterpret_cast<const float*>(&tv)[c] -
-                   (double)reinterpret_cast<const float*>(&cv)[c];
+            V[q] = reinterpret_cast<const float*>(&tv)[c] - reinterpret_cast<const float*>(&cv)[c];
           } else {
-            P[q] = (double)acc[c][q];
+            V[q] = acc[c][q];
           }
         }
         float das, dmas, ho;
-        combine<K>(P, das, dmas, ho);
+        combine<K>(V, das, dmas, ho);
         const size_t px = fbase + (size_t)j * p.nz + z;
         if (p.plane_das >= 0) p.out[px + (size_t)p.plane_das * plane] = das;
         if (p.plane_dmas >= 0) p.out[px + (size_t)p.plane_dmas * plane] = dmas;
