@@ -341,6 +341,23 @@ pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
     e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->plan_stream, cudaStreamNonBlocking);
+  // Reserve the pool's memory up front (up to the budget, at most three
+  // quarters of what is free): growing the pool while batches are in flight
+  // stalls the scheduler thread, which showed up as multi-millisecond p99
+  // latencies the first time a trace reached a new peak of buffers in flight.
+  if (e == cudaSuccess) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t want = std::min(cfg->device_budget_bytes, free_b / 4 * 3) & ~(size_t)((1 << 21) - 1);
+      void* blk = nullptr;
+      if (want > 0 && cudaMallocFromPoolAsync(&blk, want, S->pool, S->plan_stream) == cudaSuccess) {
+        cudaFreeAsync(blk, S->plan_stream);
+        e = cudaStreamSynchronize(S->plan_stream);
+      } else {
+        cudaGetLastError();  // a failed reservation only costs the warm-up
+      }
+    }
+  }
   S->slots.resize(cfg->slots);
   for (auto& s : S->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
