@@ -128,7 +128,12 @@ struct LaunchSpec {
 
 const void* bf_func(int order, bool apod, bool comp);
 void post_spec(const PostParams& p, LaunchSpec* s);
+// Radix of the first FFT pass of the in-place post kernel (the passes after
+// it are radix 8, then one radix-4 or radix-2 pass for the remainder); the
+// host builds the per-pass twiddle tables in the same order.
+__host__ __device__ constexpr int post_first_radix(int m) { return m == 1024 ? 16 : 8; }
 int post_buffers(int m);     // M-point complex buffers per team of the post kernel
+const void* post_inplace_func(int m);  // in-place kernel for M points, or nullptr
 int post_team_warps(int m);  // warps per team (column pair) of the post kernel
 void log_spec(const LogParams& p, int num_sms, LaunchSpec* s);
 

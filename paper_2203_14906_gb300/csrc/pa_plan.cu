@@ -721,6 +721,10 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   std::vector<float2> tw;
   {
     int ns = 1, rem = P->log2M;
+    if (post_inplace_func(P->M) && post_first_radix(P->M) == 16) {
+      ns = 16;  // first pass of radix 16 (sub-transform length 1: no twiddles)
+      rem -= 4;
+    }
     while (rem > 0) {
       const int lr = rem >= 3 ? 3 : rem;
       const int R = 1 << lr;

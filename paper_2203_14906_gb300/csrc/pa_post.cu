@@ -77,6 +77,44 @@ __device__ __forceinline__ void dft_regs(float2 (&x)[R]) {
   }
 }
 
+// In-register forward DFT of 16 points in natural order: 4 x 4 (n = 4a + b,
+// k = c + 4d): DFT4 over a for each b, twiddles W16^(b c), DFT4 over b for
+// each c.
+__device__ __forceinline__ void dft16_regs(float2 (&x)[16]) {
+  float2 y[4][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    float2 v[4] = {x[b], x[4 + b], x[8 + b], x[12 + b]};
+    dft_regs<4>(v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[b][c] = v[c];
+  }
+  // W16^m = cos(pi m / 8) - i sin(pi m / 8)
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  y[1][1] = cmul(y[1][1], make_float2(c1, -s1));  // m = 1
+  y[1][2] = cmul(y[1][2], make_float2(h, -h));    // m = 2
+  y[1][3] = cmul(y[1][3], make_float2(s1, -c1));  // m = 3
+  y[2][1] = cmul(y[2][1], make_float2(h, -h));    // m = 2
+  y[2][2] = cmul_mi(y[2][2]);                     // m = 4
+  y[2][3] = cmul(y[2][3], make_float2(-h, -h));   // m = 6
+  y[3][1] = cmul(y[3][1], make_float2(s1, -c1));  // m = 3
+  y[3][2] = cmul(y[3][2], make_float2(-h, -h));   // m = 6
+  y[3][3] = cmul(y[3][3], make_float2(-c1, s1));  // m = 9
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float2 v[4] = {y[0][c], y[1][c], y[2][c], y[3][c]};
+    dft_regs<4>(v);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[c + 4 * d] = v[d];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void dft_any(float2 (&x)[R]) {
+  if constexpr (R == 16) dft16_regs(x);
+  else dft_regs<R>(x);
+}
+
 // Shared buffers hold element i at i + i/8: one padding slot every eight
 // elements keeps the strided stores of the first passes (stride R elements)
 // free of multi-way bank conflicts.
@@ -256,7 +294,11 @@ struct PostShape {
   static constexpr int M = 32 * MPL;
   static constexpr int LOG2 = MPL == 2 ? 6 : MPL == 4 ? 7 : MPL == 8 ? 8 : MPL == 16 ? 9 : 10;
   static constexpr int TL = 32 * TW;                    // team lanes
-  static constexpr int G1 = M / 8;                      // radix-8 groups of a pass
+  // radix of the first pass: 16 for 1024 points (16 x 8 x 8: three passes
+  // instead of four), else 8; the passes after it follow post_pass_radix
+  static constexpr int R1 = post_first_radix(M);
+  static constexpr int LR1 = R1 == 16 ? 4 : 3;
+  static constexpr int G1 = M / R1;                     // groups of the first pass
   static constexpr int GPL = G1 >= TL ? G1 / TL : 1;    // groups per team lane
 };
 
@@ -269,17 +311,19 @@ __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* 
   for (int t = 0; t < S::GPL; ++t) {
     const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
-    float2 x[8];
+    constexpr int R = S::R1;
+    float2 x[R];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < R; ++r) {
       const int n = j + r * S::G1;
       const bool in = n < nz;
       x[r] = make_float2(in ? ca[n] : 0.f, (in && two) ? cb[n] : 0.f);
     }
-    dft_regs<8>(x);
-    float2* op = A + pidx(8 * j);  // outputs 8j + r: pidx(8j + r) = pidx(8j) + r
+    dft_any<R>(x);
+    // outputs R j + r: pidx(R j + r) = pidx(R j) + r + r / 8 (R j is a multiple of 8)
+    float2* op = A + pidx(R * j);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) op[r] = x[r];
+    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = x[r];
   }
   team_sync<TW>(tm);
 }
@@ -293,35 +337,35 @@ template <int MPL, int TW>
 __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const float* mk,
                                                  const Team& tm) {
   using S = PostShape<MPL, TW>;
-  constexpr int M = S::M;
-  float2 xa[S::GPL][8];
+  constexpr int M = S::M, R = S::R1;
+  float2 xa[S::GPL][R];
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
     const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
-    float2 xb[8];
+    float2 xb[R];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < R; ++r) {
       const int n = j + r * S::G1;
       const float2 zn = A[pidx(n)], zm = A[pidx((M - n) & (M - 1))];
       const float h = 0.5f * mk[n];
       xa[t][r] = make_float2(h * (zn.x + zm.x), -h * (zn.y - zm.y));
       xb[r] = make_float2(h * (zn.y + zm.y), h * (zn.x - zm.x));
     }
-    dft_regs<8>(xb);
-    float2* op = B + pidx(8 * j);
+    dft_any<R>(xb);
+    float2* op = B + pidx(R * j);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) op[r] = xb[r];
+    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = xb[r];
   }
   team_sync<TW>(tm);
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
     const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
-    dft_regs<8>(xa[t]);
-    float2* op = A + pidx(8 * j);
+    dft_any<R>(xa[t]);
+    float2* op = A + pidx(R * j);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) op[r] = xa[t][r];
+    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = xa[t][r];
   }
   team_sync<TW>(tm);
 }
@@ -367,7 +411,8 @@ __device__ __forceinline__ void rest_passes(float2* buf, const float2* tw, bool 
                                             float* col, int nz, float inv_m, float& mx,
                                             const Team& tm) {
   constexpr int M = 32 * MPL;
-  int ns = 8, rem = PostShape<MPL, TW>::LOG2 - 3;
+  using S = PostShape<MPL, TW>;
+  int ns = S::R1, rem = S::LOG2 - S::LR1;
   const float2* twp = tw;
   while (rem > 0) {
     const int lr = rem >= 3 ? 3 : rem;
