@@ -46,6 +46,9 @@ struct Request {
   bool finished = false;
 };
 
+// Idle gaps shorter than this before the next arrival are spun, not slept.
+constexpr double kSpinWindow = 1e-3;
+
 struct PlanEntry {
   pa_plan_t plan = nullptr;
   size_t bytes = 0;
@@ -290,9 +293,17 @@ struct pa_server_s {
         for (auto& s : slots) busy = busy || s.busy;
         if (stop && !busy) break;
         if (!busy && visible.empty()) {
-          // nothing to run or poll: sleep until the next arrival or a submit
-          if (next_arrival < 0) cv_sched.wait_for(lk, std::chrono::milliseconds(50));
-          else cv_sched.wait_for(lk, std::chrono::duration<double>(std::max(0.0, next_arrival - t)));
+          // Nothing to run or poll.  Sleep until shortly before the next
+          // arrival (or a submit); the last stretch is spun, since a timed
+          // wake-up of the thread comes tens of microseconds late.
+          if (next_arrival < 0) {
+            cv_sched.wait_for(lk, std::chrono::milliseconds(50));
+          } else if (next_arrival - t > kSpinWindow) {
+            cv_sched.wait_for(lk, std::chrono::duration<double>(next_arrival - t - kSpinWindow));
+          } else {
+            lk.unlock();
+            std::this_thread::yield();
+          }
           continue;
         }
       }
@@ -304,11 +315,9 @@ struct pa_server_s {
         }
       }
       if (!progress) {
-        // slots busy or waiting for memory: poll again shortly (bounded wait)
-        std::unique_lock<std::mutex> lk(mu);
-        double wait_s = 20e-6;
-        if (next_arrival >= 0) wait_s = std::min(wait_s, std::max(0.0, next_arrival - now()));
-        cv_sched.wait_for(lk, std::chrono::duration<double>(wait_s));
+        // slots busy or waiting for memory: poll again at once (completion is
+        // seen within a yield of the thread, not a timed wake-up later)
+        std::this_thread::yield();
       }
     }
   }
