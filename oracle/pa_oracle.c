@@ -338,8 +338,8 @@ static double raised_cos_band(double f, double lo, double hi, double roll) {
 }
 
 int or_post_mask(const or_desc* d, int even_order, int m, double* h) {
-  /* Band-pass (reading: "applied at the appropriate frequency range",
-   * Section 3): a raised-cosine band around f0 for DAS and odd orders, around
+  /* Band-pass (reading: Section 3 names a band-pass filter but gives no
+   * band): a raised-cosine band around f0 for DAS and odd orders, around
    * 2 f0 for even orders, roll-off 0.25 f0 each side, clipped at the axial
    * Nyquist rate c / (2 dz).  Times the analytic-signal mask of the Hilbert
    * transform: 1 at DC and M/2, 2 on positive bins, 0 on negative bins. */
