@@ -227,8 +227,9 @@ def oracle_run(wl, rf64_frames, k, budget_s):
     pairs = wl["nx"] * wl["nz"] * wl["n_elem"]
     t0 = time.perf_counter()
     done = 0
-    for f in range(rf64_frames.shape[0]):
-        oracle.frame(wl, rf64_frames[f], order_k=k, stages=("raw", "env", "log"))
+    nf = rf64_frames.shape[0]
+    while True:  # cycle through the step's frames until the budget is spent
+        oracle.frame(wl, rf64_frames[done % nf], order_k=k, stages=("raw", "env", "log"))
         done += 1
         if time.perf_counter() - t0 >= budget_s:
             break
@@ -563,7 +564,8 @@ def run_ours(args):
         "share_of_step": bf_ms / (sum(v[0] for v in prof.values()) or 1),
         "kernels_ms_per_launch": {kk: (v[0] / max(v[1], 1)) for kk, v in prof.items()},
     }
-    launches = int(sum(v[1] for v in prof.values()))
+    # the three kernels profiled per launch sequence, plus its clearing kernel
+    launches = int(sum(v[1] for v in prof.values()) + prof["bf_fused"][1])
 
     # ---- end to end through the host-buffer ABI call
     desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype="f32", max_batch=F)
