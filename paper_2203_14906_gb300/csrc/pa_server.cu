@@ -148,15 +148,18 @@ struct pa_server_s {
     return any;
   }
 
-  // Destroy least recently used idle plans until `need` more bytes fit.
-  void evict_for(size_t need) {
+  // Destroy least recently used idle plans until `need` more bytes fit and,
+  // when a plan is about to be added, the resident plans stay within
+  // max_plans.
+  void evict_for(size_t need, bool adding_plan) {
     for (;;) {
       size_t cur;
       {
         std::lock_guard<std::mutex> lk(mu);
         cur = in_use;
       }
-      const bool over_count = (int)plans.size() > std::max(1, cfg.max_plans);
+      const bool over_count =
+          (int)plans.size() + (adding_plan ? 1 : 0) > std::max(1, cfg.max_plans);
       if (cur + need <= cfg.device_budget_bytes && !over_count) return;
       auto victim = plans.end();
       for (auto it = plans.begin(); it != plans.end(); ++it) {
@@ -192,7 +195,7 @@ struct pa_server_s {
         if (pa_plan_footprint(&d, 0, &plan_bytes) != PA_OK) plan_bytes = 0;
       }
       const size_t need = buf_rf + buf_out + plan_bytes;
-      evict_for(need);
+      evict_for(need, pit == plans.end());
       {
         std::lock_guard<std::mutex> lk(mu);
         if (in_use + need > cfg.device_budget_bytes) return false;  // wait for memory

@@ -130,3 +130,32 @@ def test_timeout_and_rejections():
         with pytest.raises(PAError) as e:
             small.submit(pa.make_desc(wl, order_k=k), rf.data_ptr(), out.data_ptr())
         assert e.value.status == PA_ENOMEM
+
+
+def test_plan_cache_eviction_keeps_results():
+    """max_plans = 1 with requests alternating between two geometries: every
+    request evicts the other plan and rebuilds its own; results stay equal to
+    a direct call."""
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300.serving import Server
+
+    (wa, ka), (wb, kb) = _mix_workloads()[0], _mix_workloads()[1]
+    fa, fb = _frame(wa, 5), _frame(wb, 6)
+    want = {}
+    for key, (w, k, f) in {"a": (wa, ka, fa), "b": (wb, kb, fb)}.items():
+        with pa.Plan(pa.make_desc(w, order_k=k)) as plan:
+            want[key] = pa.beamform(plan, f.cuda()[None].view(torch.bfloat16), LOG).cpu()[0]
+    outs = []
+    with Server(budget_bytes=2 << 30, slots=1, max_batch=1, max_plans=1) as srv:
+        for i in range(6):
+            key, (w, k, f) = ("a", (wa, ka, fa)) if i % 2 == 0 else ("b", (wb, kb, fb))
+            o = _out(pa, w, k)
+            r = srv.wait(srv.submit(pa.make_desc(w, order_k=k), f.data_ptr(), o.data_ptr()))
+            assert r["status"] == 0
+            outs.append((key, o))
+        st = srv.stats()
+    assert st["plans_resident"] <= 1 and st["completed"] == 6
+    for key, o in outs:
+        assert torch.equal(o, want[key]), key
