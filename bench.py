@@ -185,11 +185,17 @@ def sm_max_mhz():
 
 def kernel_source_hash():
     """Hash of the fused kernel's sources and of the plan code that sizes its
-    launches (tiles, chunks, shared memory)."""
+    launches (tiles, chunks, shared memory), with comments and blank space
+    removed, so that a change of wording does not void a measurement."""
+    import re
+
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
         if f.startswith("pa_bf") or f in ("pa_internal.cuh", "pa_plan.cu"):
-            h.update(open(os.path.join(CSRC, f), "rb").read())
+            src = open(os.path.join(CSRC, f)).read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
+            h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

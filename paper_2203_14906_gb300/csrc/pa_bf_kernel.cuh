@@ -1,6 +1,6 @@
 // pa_bf_kernel.cuh -- fused delay-gather + interpolation + signed root +
-// power-sum kernel with an FP64 Newton-identity epilogue (Sections 2.1-2.3:
-// Eq. 1 DAS, Eq. 3 real-time DMAS, Eqs. 7-9 O(N) DMAS-k).
+// power-sum kernel with an FP64 e_k epilogue (Sections 2.1-2.3: Eq. 1 DAS,
+// Eq. 3 real-time DMAS, Eqs. 7-9 O(N) DMAS-k).
 //
 // Work decomposition (one persistent CTA loop over work items):
 //   item   = (pixel tile, residue group, frame), taken from an atomic counter
@@ -16,8 +16,8 @@
 //            reproduces the rule "s = 0 when a tap leaves the record".
 // Per pair the arithmetic is FP32: interpolation, apodisation, one MUFU
 // lg2/ex2 (or rsqrt) pair for the roots, power sums; Kahan-compensated
-// sums are folded every kFoldBlocks*kC channels when requested.  The power
-// sums p_1..p_k are turned into e_k by Newton's identities in FP64.
+// sums are folded every kFoldBlocks*kC channels when requested.  Per pixel,
+// the power sums p_1..p_k are turned into e_k in FP64 (see combine).
 #pragma once
 
 #include <cuda_bf16.h>
