@@ -89,6 +89,10 @@ def dist_setup(args):
         import torch.distributed as dist
 
         backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)  # each rank's collectives on its own GPU
         dist.init_process_group(backend=backend)
         pg = dist
     return ws, rank, local, pg
