@@ -247,6 +247,37 @@ def oracle_run(wl, rf64_frames, k, budget_s):
     return done, pairs * done / dt / 1e9, dt, oracle.get_threads()
 
 
+def oracle_timing():
+    """FP64 oracle pairs/s per workload: cfg1 and cfg2 frames on all host
+    cores and on one core, one cfg5 frame on all cores; median of the runs
+    after one warm-up (5 runs; 3 for the slow one-core cfg2 frame)."""
+    import oracle
+    import synth
+
+    oracle.build()
+    n_all = oracle.get_threads()
+    out = {}
+    for name, seed, cores_list in (("cfg1", 1, (n_all, 1)), ("cfg2", 11, (n_all, 1)),
+                                   ("cfg5", 41, (n_all,))):
+        wl = synth.workload(name)
+        rf = synth.quantize(synth.make_frame(wl, seed, 0), "f32")[1]
+        pairs = wl["nx"] * wl["nz"] * wl["n_elem"]
+        for cores in cores_list:
+            oracle.set_threads(cores)
+            runs = 3 if (cores == 1 and name != "cfg1") else 5
+            oracle.frame(wl, rf, order_k=wl["order_k"])
+            ts = []
+            for _ in range(runs):
+                t0 = time.perf_counter()
+                oracle.frame(wl, rf, order_k=wl["order_k"])
+                ts.append(time.perf_counter() - t0)
+            out[f"{name}_{cores}core{'s' if cores > 1 else ''}"] = {
+                "gpixel_ch_per_s": pairs / float(np.median(ts)) / 1e9,
+                "ms_per_frame": float(np.median(ts)) * 1e3, "runs": runs, "k": wl["order_k"]}
+    oracle.set_threads(n_all)
+    return out
+
+
 def run_reference(args):
     ws, rank, local, pg = dist_setup(args)
     if rank != 0:
@@ -556,6 +587,7 @@ def run_ours(args):
     barrier()
     t_tot = max_over_ranks(sum(times), pg, dev)
     value = job_value(pairs_step, ws, args.steps, t_tot)
+    step_median_ms = float(np.median(times)) * 1e3
 
     # roofline of the dominant kernel (the fused beamformer)
     bf_ms, bf_n = prof["bf_fused"]
@@ -623,6 +655,7 @@ def run_ours(args):
                 "against": "FP64 oracle on the unquantised RF, frame 0",
             }
             extras["metrics_form"] = metrics_bench(pa, torch, wl, args, frames64, stream, flush)
+            extras["oracle_timing"] = oracle_timing()
             extras["throughput_batch"] = throughput_batch(pa, torch, args, stream, flush)
             done, v_cpu, dt, cores = oracle_run(wl, frames64, k, args.cpu_seconds)
             extras["cpu_baseline"] = {
@@ -644,6 +677,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_tot / args.steps * 1e3,
+            "ms_per_step_median": step_median_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded point + line absorbers, 3% noise; cfg2 recipe)",
             "config": config_dict(args, wl), "clocks": clocks, "e2e": e2e,
