@@ -306,7 +306,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded cfg2 recipe)",
-        "config": config_dict(args, wl, {"frames_per_step": 1}),
+        "config": config_dict(args, wl, {"frames_per_step": 1,
+                                         "l2": "not applicable (FP64 oracle on the host cores)"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
