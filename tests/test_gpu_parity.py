@@ -301,3 +301,15 @@ def test_chunk_length_does_not_change_bits(monkeypatch):
             assert info2["chunk_steps"] <= int(steps)
             assert info2["device_error_flags"] == 0
             assert np.array_equal(out, ref), (w["name"], k, dt, steps)
+
+
+def test_off_centre_window():
+    """An image window narrower than the aperture, off its centre and
+    starting below the surface (x in [-4.5, 7.5] mm, z in [6, 18] mm):
+    lattice offsets of both signs at the window edges, k = 3 and 4."""
+    wl = synth.workload("cfg1", nx=80, nz=96, x0_m=-4.5e-3, x1_m=7.5e-3, z0_m=6e-3, z1_m=18e-3)
+    rf = _frames(wl, [3])
+    for k in (3, 4):
+        out, info, deq = run_gpu(wl, rf, k)
+        assert info["lattice_m"] == 2 and info["device_error_flags"] == 0
+        assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"window k={k}")
