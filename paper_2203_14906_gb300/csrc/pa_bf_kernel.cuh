@@ -129,28 +129,30 @@ __device__ __forceinline__ void combine(const float* V, float& das, float& dmas,
   } else if constexpr (K == 2) {
     ho = dmas;
   } else if constexpr (K == 3) {
-    // e3 = (p1^3 - 3 p1 p2 + 2 p3) / 6 (p1^2 is exact in FP64, each FMA rounds once)
-    const double p1 = V[3], p2 = V[4], p3 = V[0];
+    // e3 = (p1^3 - 3 p1 p2 + 2 p3) / 6.  p1^2 is exact in FP64 and each FMA
+    // rounds once; scalings by powers of two are exact in FP32 and are done
+    // there, as is the final division (the result is FP32): fewer FP64 ops.
+    const double p1 = V[3], p2 = V[4], p3x2 = 2.0f * V[0];
     const double t = fma(p1, p1, -3.0 * p2);
-    ho = (float)(fma(t, p1, 2.0 * p3) * (1.0 / 6.0));
+    ho = (float)fma(t, p1, p3x2) * (1.0f / 6.0f);
   } else if constexpr (K == 4) {
     // e4 = (p1^4 - 6 p1^2 p2 + 3 p2^2 + 8 p1 p3 - 6 p4) / 24, p4 = sum |s| (even k)
-    const double p1 = V[3], p2 = V[4], p3 = V[5], p4 = V[2];
+    const double p1 = V[3], p2 = V[4], p3x8 = 8.0f * V[5], p4 = V[2];
     const double t = p1 * p1;
     double e = fma(-6.0, p2, t) * t;
-    e = fma(8.0 * p1, p3, e);
+    e = fma(p1, p3x8, e);
     e = fma(3.0 * p2, p2, e);
-    ho = (float)(fma(-6.0, p4, e) * (1.0 / 24.0));
+    ho = (float)fma(-6.0, p4, e) * (1.0f / 24.0f);
   } else if constexpr (K == 5) {
     // e5 = (p1 (p1^4 - 10 p1^2 p2 + 15 p2^2 - 30 p4) + 20 p3 (p1^2 - p2) + 24 p5) / 120,
-    // p5 = sum s (odd k)
-    const double p1 = V[3], p2 = V[4], p3 = V[5], p4 = V[6], p5 = V[0];
+    // p5 = sum s (odd k); 8 p5 is exact in FP32 (24 p5 = 3 (8 p5))
+    const double p1 = V[3], p2 = V[4], p3 = V[5], p4 = V[6], p5x8 = 8.0f * V[0];
     const double t = p1 * p1;
     double e = fma(-10.0, p2, t) * t;
     e = fma(15.0 * p2, p2, e);
     e = fma(-30.0, p4, e) * p1;
     e = fma(20.0 * p3, t - p2, e);
-    ho = (float)(fma(24.0, p5, e) * (1.0 / 120.0));
+    ho = (float)fma(3.0, p5x8, e) * (1.0f / 120.0f);
   } else {
     double p[K + 1];
 #pragma unroll
