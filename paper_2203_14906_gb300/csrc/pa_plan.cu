@@ -1097,7 +1097,7 @@ pa_status pa_plan_footprint(const pa_plan_desc* desc, int32_t n_frames, size_t* 
   P.d = *desc;
   configure(&P);
   size_t b = table_bytes(&P);
-  b += (2 + (size_t)P.d.max_batch * 3) * sizeof(int);
+  b += (3 + (size_t)P.d.max_batch * 3) * sizeof(int);  // scratch, as pa_plan allocates it
   const size_t elt = desc->rf_dtype == PA_RF_F32 ? 4 : 2;
   b += (size_t)n_frames * desc->n_elem * desc->n_samples * elt;
   b += (size_t)n_frames * 3 * P.n_out * desc->nx * desc->nz * sizeof(float);
