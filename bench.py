@@ -535,7 +535,9 @@ def serving_bench(pa, args, rf_dtype, comp):
         for t in warm:
             srv.wait(t)
         st0 = srv.stats()
-        t0 = srv.now() + 0.05
+        # every request is queued before the first arrival (the submit loop
+        # cannot lag the trace), then the server replays the arrival times
+        t0 = srv.now() + 0.5
         tickets = [srv.submit(d, rf.data_ptr(), ring[i % ring_n].data_ptr(), t0 + t_arr)
                    for i, (t_arr, d, rf, _) in enumerate(reqs)]
         res = [srv.wait(t) for t in tickets]
