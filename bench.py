@@ -633,6 +633,18 @@ def run_ours(args):
            "call": "pa_beamform_host (pinned host buffers)", "steps": e2e_steps}
 
     extras = {}
+    # serving first: the CPU-heavy oracle legs below would compete with the
+    # server's scheduler thread for host cores
+    if not args.no_serving and rank == 0:
+        extras["serving"] = {
+            "workload": (f"cfg4 mix: {args.serve_requests} requests, Poisson {args.serve_rate:g} "
+                         "frames/s; N in {64,128,256}, Ns in {1024,2048,4096} @ 40 MHz, grid "
+                         "{256,512,1024}^2, k uniform in 2..5; DAS+DMAS+DMAS-k log images "
+                         "returned to pinned host memory"),
+            "bf16_kahan": serving_bench(pa, args, "bf16", 1),
+            "fp32": serving_bench(pa, args, "f32", 0),
+        }
+
     if not args.no_extras:
         # reduced-precision form on the same workload: BF16 RF + Kahan sums
         t_bf, prof_bf, _ = time_form(pa, torch, wl, args, "bf16", 1, frames64, stream, flush)
@@ -666,16 +678,6 @@ def run_ours(args):
                 "sample": (f"{done} whole frame(s) of the workload (raw+env+log, k={k}), "
                            f"{dt:.1f} s, FP64, OpenMP over image columns"),
             }
-    if not args.no_serving and rank == 0:
-        extras["serving"] = {
-            "workload": (f"cfg4 mix: {args.serve_requests} requests, Poisson {args.serve_rate:g} "
-                         "frames/s; N in {64,128,256}, Ns in {1024,2048,4096} @ 40 MHz, grid "
-                         "{256,512,1024}^2, k uniform in 2..5; DAS+DMAS+DMAS-k log images "
-                         "returned to pinned host memory"),
-            "bf16_kahan": serving_bench(pa, args, "bf16", 1),
-            "fp32": serving_bench(pa, args, "f32", 0),
-        }
-
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
