@@ -969,6 +969,13 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
   const cudaKernelNodeParams kq = node_params(c.sq, aq);
   const cudaKernelNodeParams kl = node_params(c.sl, al);
   if (!ge) {
+    // bounded cache: drop the oldest graph once 32 shapes are held (callers
+    // that vary the batch size every call would otherwise grow it forever)
+    if (P->graphs.size() >= 32) {
+      cudaGraphExecDestroy(P->graphs.front().exec);
+      cudaGraphDestroy(P->graphs.front().graph);
+      P->graphs.erase(P->graphs.begin());
+    }
     pa_plan_s::GraphEntry g;
     g.nf = nf;
     g.stages = stages;

@@ -313,3 +313,22 @@ def test_off_centre_window():
         out, info, deq = run_gpu(wl, rf, k)
         assert info["lattice_m"] == 2 and info["device_error_flags"] == 0
         assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"window k={k}")
+
+
+def test_graph_cache_beyond_its_bound():
+    """Forty different batch sizes on one plan (the plan keeps at most 32
+    launch graphs, dropping the oldest): every call still gives the bits of a
+    direct launch."""
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+
+    wl = synth.workload("cfg1", nx=64, nz=32, z1_m=10e-3)
+    rf = torch.from_numpy(synth.quantize(_frames(wl, list(range(40))), "f32")[0]).cuda()
+    with pa.Plan(pa.make_desc(wl, order_k=3, max_batch=40)) as plan:
+        plan.use_graph(False)
+        ref = pa.beamform(plan, rf, 7)
+        plan.use_graph(True)
+        for n in list(range(1, 41)) + [3, 17, 40]:
+            out = pa.beamform(plan, rf[:n].contiguous(), 7)
+            assert torch.equal(out, ref[:n]), n
