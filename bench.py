@@ -188,14 +188,15 @@ def sm_max_mhz():
 
 
 def kernel_source_hash():
-    """Hash of the fused kernel's sources and of the plan code that sizes its
-    launches (tiles, chunks, shared memory), with comments and blank space
-    removed, so that a change of wording does not void a measurement."""
+    """Hash of the fused kernel's sources, with comments and blank space
+    removed, so that a change of wording does not void a measurement.  The
+    launch configuration the plan picks is checked separately
+    (LAUNCH_FIELDS)."""
     import re
 
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
-        if f.startswith("pa_bf") or f in ("pa_internal.cuh", "pa_plan.cu"):
+        if f.startswith("pa_bf") or f == "pa_internal.cuh":
             src = open(os.path.join(CSRC, f)).read()
             src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
             src = re.sub(r"//[^\n]*", " ", src)
@@ -203,15 +204,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kind):
+# Plan facts that fix the fused kernel's launch (grid, block, shared memory).
+LAUNCH_FIELDS = ("threads", "blocks_per_sm", "window", "chunk_steps", "tile_x", "tile_z",
+                 "tma_staging")
+
+
+def measured_traffic(kind, info=None):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+    summary, only if it was taken on the current kernel source and the plan
+    launches it the same way."""
     p = os.path.join(ROOT, "profiles", "bf_fused_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         if d.get("kernel_hash") != kernel_source_hash():
+            return None
+        launch = d.get("launch", {})
+        if info is not None and any(launch.get(f) != info.get(f) for f in LAUNCH_FIELDS):
             return None
         return d.get(kind)
     except Exception:
@@ -602,7 +612,7 @@ def run_ours(args):
     peak = n_sm * 128 * mhz * 1e6 / 1e12
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s (FP32 pipe, FMA=1)",
-        "frac": achieved / peak, "traffic": measured_traffic("dram_bytes_per_launch"),
+        "frac": achieved / peak, "traffic": measured_traffic("dram_bytes_per_launch", info),
         "kernel": "k_bf_fused", "ops_per_pair": opp,
         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {mhz:g} MHz ({mhz_src})",
         "kernel_ms_per_launch": bf_s * 1e3,
