@@ -630,8 +630,14 @@ def run_ours(args):
         out_h = torch.empty(plan.out_shape(F, pa.PA_STAGE_LOG), dtype=torch.float32).pin_memory()
         for _ in range(max(1, args.warmup)):
             pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
+        # the plan times candidate chunk schedules on its first calls of a shape
+        for _ in range(200):
+            chunks, state = plan.host_schedule(F, pa.PA_STAGE_LOG)
+            if state != 1:
+                break
+            pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
         barrier()
-        e2e_steps = max(1, min(args.steps, 10))
+        e2e_steps = max(1, min(args.steps, 50))
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             pa.beamform_host(plan, rf_h, pa.PA_STAGE_LOG, out=out_h)
@@ -640,7 +646,8 @@ def run_ours(args):
     e2e = {"value": job_value(pairs_step, ws, e2e_steps, te), "unit": UNIT,
            "h2d_bytes_per_step": int(rf_h.numel() * rf_h.element_size()),
            "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size()),
-           "call": "pa_beamform_host (pinned host buffers)", "steps": e2e_steps}
+           "call": "pa_beamform_host (pinned host buffers)", "steps": e2e_steps,
+           "chunks": chunks}
 
     extras = {}
     # serving first: the CPU-heavy oracle legs below would compete with the

@@ -174,9 +174,11 @@ pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
  * return.  Copies overlap with compute across frames.  Pinned (page-locked)
  * host memory gives the full copy rate.  Device staging buffers are
  * allocated on first use and owned by the plan.
- * Frames are processed in chunks (short first and last chunks, so the
- * first upload and the last download overlap as little compute as possible)
- * rotating over three device buffer sets and streams.
+ * Frames are processed in chunks rotating over three device buffer sets and
+ * streams; the launch sequence of a chunk starts after the previous chunk's
+ * (neighbouring launches do not share the GPU), while uploads and downloads
+ * overlap them.  The chunk schedule per (n_frames, stages) is tuned over the
+ * first calls of that shape (pa_plan_host_schedule).
  * Errors: as pa_beamform, plus PA_ETIMEOUT when a thread block of the fused
  * kernel gave up waiting for its TMA staging copies (a bounded wait of about
  * a second; the block stops early, so the output is incomplete;
@@ -186,6 +188,65 @@ pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
 pa_status pa_beamform_host(pa_plan_t plan, const void* rf_host,
                            int32_t n_frames, float* out_host, uint32_t stages,
                            void* cuda_stream);
+
+/*
+ * Host-path chunk schedules.  pa_beamform_host splits its frames into chunks
+ * (see the pipeline model below).  For each (n_frames, stages) the plan first
+ * tries a few candidate schedules, each on two calls, timing every call on
+ * the host, and then keeps the fastest; results are identical whatever the
+ * schedule.  pa_plan_set_host_schedule fixes the schedule of one
+ * (n_frames, stages) instead: chunks[0..n_chunks) are frame counts, each in
+ * 1..max_batch, summing to n_frames (n_chunks = 0 returns that shape to
+ * tuning).  pa_plan_host_schedule reports the schedule the next call of that
+ * shape will use in chunks[0..*n_chunks) (max_chunks entries of room) and
+ * *state: 1 still trying candidates, 2 tuned, 3 set by the caller.
+ * Tuning: every candidate is timed once, then the three fastest once more;
+ * a call that had to build a CUDA graph or grow the plan's staging buffers
+ * is not counted, and its candidate runs again.
+ * Errors: PA_EINVAL for null pointers, n_frames < 1, an invalid stages mask
+ * or an invalid schedule, or too little room.
+ */
+pa_status pa_plan_set_host_schedule(pa_plan_t plan, int32_t n_frames, uint32_t stages,
+                                    const int32_t* chunks, int32_t n_chunks);
+pa_status pa_plan_host_schedule(pa_plan_t plan, int32_t n_frames, uint32_t stages,
+                                int32_t* chunks, int32_t max_chunks, int32_t* n_chunks,
+                                int32_t* state);
+
+/*
+ * Pipeline model of the host path (host logic; no GPU involved).  Per chunk
+ * of f frames: an upload of f * upload_us, the launch sequence taking
+ * f * kernel_us * ((1 - wave_share) + wave_share * ceil(w) / w) + launch_us
+ * with w = f * items_per_frame / resident (the waves of the persistent fused
+ * kernel; wave_share = 1 when every work item costs the same, less when
+ * cheaper items fill the last wave), and a download of f * download_us.  Uploads,
+ * launch sequences and downloads each run one at a time in chunk order; the
+ * chunks rotate over n_sets buffer sets, and a chunk's upload waits for the
+ * download that last used its set.  pa_pipe_time gives the makespan (us) of
+ * a schedule; pa_pipe_schedule writes the schedule of least makespan among a
+ * searched family (a short first chunk, equal middle chunks, a tail of
+ * shrinking chunks; chunks of at most max_chunk frames) to
+ * chunks[0..*n_chunks), max_chunks entries of room.  pa_beamform_host draws
+ * its candidate schedules from it over a range of kernel_us, launch_us and
+ * wave_share.
+ * Errors: PA_EINVAL for null pointers, items_per_frame or resident < 1,
+ * n_sets outside 1..8, chunks of < 1 frame, n_frames or max_chunk < 1, or
+ * too little room.
+ */
+typedef struct pa_pipe_model {
+  int32_t items_per_frame;  /* work items of the fused kernel per frame */
+  int32_t resident;         /* thread blocks of the fused kernel resident at once */
+  int32_t n_sets;           /* device buffer sets (streams), 1..8 */
+  int32_t reserved;         /* 0 */
+  double upload_us;         /* per frame */
+  double kernel_us;         /* per frame, at whole waves */
+  double download_us;       /* per frame */
+  double launch_us;         /* per chunk */
+  double wave_share;        /* share of kernel_us that runs in whole waves, 0..1 */
+} pa_pipe_model;
+pa_status pa_pipe_time(const pa_pipe_model* model, const int32_t* chunks, int32_t n_chunks,
+                       double* us);
+pa_status pa_pipe_schedule(const pa_pipe_model* model, int32_t n_frames, int32_t max_chunk,
+                           int32_t* chunks, int32_t max_chunks, int32_t* n_chunks);
 
 /*
  * Launch mode.  By default (enable = 1) each pa_beamform launch sequence
@@ -394,7 +455,7 @@ const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);
 /* ABI version (major * 100 + minor). */
-int32_t pa_version(void);  /* 102: pa_plan_info.chunk_steps */
+int32_t pa_version(void);  /* 103: host-path chunk schedules */
 
 #ifdef __cplusplus
 }

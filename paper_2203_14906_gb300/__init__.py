@@ -22,5 +22,7 @@ from ._native import (  # noqa: F401
     load,
     make_desc,
     make_grid,
+    pipe_schedule,
+    pipe_time,
 )
 from .torch_api import beamform, beamform_host, image_metrics  # noqa: F401

@@ -35,6 +35,10 @@ EXPORTS = (
     "pa_plan_use_graph",
     "pa_plan_profile",
     "pa_plan_profile_read",
+    "pa_plan_set_host_schedule",
+    "pa_plan_host_schedule",
+    "pa_pipe_time",
+    "pa_pipe_schedule",
     "pa_image_metrics",
     "pa_destroy",
     "pa_status_str",
@@ -68,6 +72,22 @@ class PlanDesc(ctypes.Structure):
         ("dyn_range_db", ctypes.c_double),
         ("compensated", ctypes.c_int32),
         ("interp", ctypes.c_int32),
+    ]
+
+
+class PipeModel(ctypes.Structure):
+    """Pipeline model of the host-buffer path (see pa_pipe_model)."""
+
+    _fields_ = [
+        ("items_per_frame", ctypes.c_int32),
+        ("resident", ctypes.c_int32),
+        ("n_sets", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("upload_us", ctypes.c_double),
+        ("kernel_us", ctypes.c_double),
+        ("download_us", ctypes.c_double),
+        ("launch_us", ctypes.c_double),
+        ("wave_share", ctypes.c_double),
     ]
 
 
@@ -197,6 +217,16 @@ def load(checked: bool = False, build: bool = True):
         L.pa_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
         L.pa_plan_profile_read.restype = ctypes.c_int
+        I32P = ctypes.POINTER(ctypes.c_int32)
+        L.pa_plan_set_host_schedule.argtypes = [vp, i32, u32, I32P, i32]
+        L.pa_plan_set_host_schedule.restype = ctypes.c_int
+        L.pa_plan_host_schedule.argtypes = [vp, i32, u32, I32P, i32, I32P, I32P]
+        L.pa_plan_host_schedule.restype = ctypes.c_int
+        L.pa_pipe_time.argtypes = [ctypes.POINTER(PipeModel), I32P, i32,
+                                   ctypes.POINTER(ctypes.c_double)]
+        L.pa_pipe_time.restype = ctypes.c_int
+        L.pa_pipe_schedule.argtypes = [ctypes.POINTER(PipeModel), i32, i32, I32P, i32, I32P]
+        L.pa_pipe_schedule.restype = ctypes.c_int
         L.pa_log_compress_noalloc.argtypes = [vp, i32, ctypes.c_int64, ctypes.c_float, vp, vp]
         L.pa_log_compress_noalloc.restype = ctypes.c_int
         L.pa_image_metrics.argtypes = [ctypes.POINTER(Grid), vp, i32, ctypes.POINTER(Roi), i32,
@@ -293,6 +323,23 @@ class Plan:
         check(self._L, self._L.pa_beamform_host(self._h, rf_host_ptr, int(n_frames), out_host_ptr,
                                                 int(stages), _stream_handle(stream)))
 
+    def set_host_schedule(self, n_frames: int, stages: int, chunks):
+        """Fix the chunk schedule of beamform_host for (n_frames, stages);
+        an empty list returns that shape to tuning."""
+        c = (ctypes.c_int32 * max(1, len(chunks)))(*[int(x) for x in chunks])
+        check(self._L, self._L.pa_plan_set_host_schedule(self._h, int(n_frames), int(stages), c,
+                                                         len(chunks)))
+
+    def host_schedule(self, n_frames: int, stages: int):
+        """(chunks, state) the next beamform_host call of this shape uses;
+        state 1 tuning, 2 tuned, 3 set by the caller."""
+        room = max(1, int(n_frames))
+        c = (ctypes.c_int32 * room)()
+        n, st = ctypes.c_int32(), ctypes.c_int32()
+        check(self._L, self._L.pa_plan_host_schedule(self._h, int(n_frames), int(stages), c, room,
+                                                     ctypes.byref(n), ctypes.byref(st)))
+        return [c[i] for i in range(n.value)], st.value
+
     def use_graph(self, enable: bool = True):
         """Launch each sequence as a CUDA graph (default) or kernel by kernel."""
         check(self._L, self._L.pa_plan_use_graph(self._h, int(bool(enable))))
@@ -324,6 +371,37 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _pipe_model(items_per_frame, resident, upload_us, kernel_us, download_us, launch_us=8.0,
+                wave_share=1.0, n_sets=3) -> PipeModel:
+    return PipeModel(items_per_frame=int(items_per_frame), resident=int(resident),
+                     n_sets=int(n_sets), reserved=0, upload_us=float(upload_us),
+                     kernel_us=float(kernel_us), download_us=float(download_us),
+                     launch_us=float(launch_us), wave_share=float(wave_share))
+
+
+def pipe_time(chunks, checked: bool = False, **model) -> float:
+    """Makespan (us) of a chunk schedule under the host-path pipeline model
+    (keyword arguments as the fields of PipeModel; no GPU needed)."""
+    L = load(checked)
+    m = _pipe_model(**model)
+    c = (ctypes.c_int32 * max(1, len(chunks)))(*[int(x) for x in chunks])
+    us = ctypes.c_double()
+    check(L, L.pa_pipe_time(ctypes.byref(m), c, len(chunks), ctypes.byref(us)))
+    return us.value
+
+
+def pipe_schedule(n_frames: int, max_chunk: int, checked: bool = False, **model) -> list:
+    """Least-makespan schedule of the searched family (no GPU needed)."""
+    L = load(checked)
+    m = _pipe_model(**model)
+    room = max(1, int(n_frames))
+    c = (ctypes.c_int32 * room)()
+    n = ctypes.c_int32()
+    check(L, L.pa_pipe_schedule(ctypes.byref(m), int(n_frames), int(max_chunk), c, room,
+                                ctypes.byref(n)))
+    return [c[i] for i in range(n.value)]
 
 
 def footprint(desc: PlanDesc, n_frames: int, checked: bool = False) -> int:

@@ -3,6 +3,7 @@
 // delays are computed once and kept resident in device memory), per-tile RF
 // windows, post-filter masks, and the launch sequence of pa_beamform.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <cudaTypedefs.h>
 
 #include "pa_internal.cuh"
+#include "pa_schedule.h"
 
 using namespace pa;
 
@@ -101,6 +103,26 @@ struct pa_plan_s {
   size_t h_rf_bytes = 0, h_out_bytes = 0;
   cudaStream_t hs[kHostSets] = {nullptr, nullptr, nullptr};
   cudaEvent_t h_ev = nullptr;
+  cudaEvent_t h_done[kHostSets] = {nullptr, nullptr, nullptr};
+  // chunk schedules of the host path, per (frames, stages): every candidate
+  // timed once, the three fastest once more, then the fastest kept
+  struct HostTune {
+    int nf = 0;
+    uint32_t stages = 0;
+    std::vector<std::vector<int32_t>> cand;
+    std::vector<double> best_ms;  // < 0: not measured yet
+    std::vector<int> order;       // candidates in the order they are timed
+    size_t pos = 0;
+    int attempts = 0;             // uncounted (cold) calls of order[pos]
+    bool second_round = false;
+    int chosen = -1;              // index into cand once tuned
+    std::vector<int32_t> fixed;   // set by pa_plan_set_host_schedule
+    const std::vector<int32_t>& current() const {
+      return !fixed.empty() ? fixed : cand[chosen >= 0 ? chosen : order[pos]];
+    }
+  };
+  std::vector<HostTune> tunes;
+  long long graph_builds = 0;  // executable graphs instantiated so far
   // CUDA graphs of the launch sequence, one per (frames, stages)
   struct GraphEntry {
     int nf = 0;
@@ -493,6 +515,8 @@ void free_plan(pa_plan_s* P) {
   for (int s = 0; s < kHostSets; ++s)
     if (P->hs[s]) cudaStreamDestroy(P->hs[s]);
   if (P->h_ev) cudaEventDestroy(P->h_ev);
+  for (int s = 0; s < kHostSets; ++s)
+    if (P->h_done[s]) cudaEventDestroy(P->h_done[s]);
   for (auto& g : P->graphs) {
     cudaGraphExecDestroy(g.exec);
     cudaGraphDestroy(g.graph);
@@ -996,6 +1020,7 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
       return fail(PA_ECUDA, "graph build: %s", cudaGetErrorString(e));
     }
     g.graph = graph;
+    ++P->graph_builds;
     P->graphs.push_back(g);
     ge = &P->graphs.back();
   } else {
@@ -1018,6 +1043,99 @@ pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t s
   if (ps != PA_OK) return ps;
   if (P->use_graph && !P->prof) return launch_graph(P, c, nf, stages, st);
   return launch_direct(P, c, st);
+}
+
+// Tapered schedule: short first and last chunks (the first upload and the
+// last download overlap no compute), evenly sized middle chunks, none above
+// cap frames.
+std::vector<int32_t> taper_schedule(int n, int cap) {
+  std::vector<int32_t> sched;
+  const int edge = std::min(cap, std::max(1, n / 5));
+  const int mid = n - 2 * edge;
+  if (mid < 0) {  // one or two frames
+    for (int f = 0; f < n; ++f) sched.push_back(1);
+    return sched;
+  }
+  sched.push_back(edge);
+  const int nm = mid == 0 ? 0 : std::max(2, (mid + cap - 1) / cap);
+  for (int q = 0; q < nm; ++q) {
+    const int c = (mid * (q + 1)) / nm - (mid * q) / nm;
+    if (c > 0) sched.push_back(c);
+  }
+  sched.push_back(edge);
+  return sched;
+}
+
+// Host-path link rate assumed by the candidate schedules: about 200 GB/s each
+// way between pinned Grace memory and the GPU (measured 206 GB/s up, 192 GB/s
+// down on GB300).
+constexpr double kLinkBytesPerUs = 2.0e5;
+
+// The tuning state of one (frames, stages) shape, created on first use with
+// its candidates: the tapered schedule and the pipeline model's best
+// schedules for kernel times of 0.6x to 2.8x the per-frame copy time,
+// per-chunk launch costs of 8 and 40 us and wave shares of 0 and 1.  None of
+// these is known in advance (measured on GB300: 38 us per chunk and no wave
+// effect for 512 x 512 images at k = 3; about 50 us and a full wave effect
+// at 1024 x 1024, k = 4); the tuning calls measure the outcome.
+pa_plan_s::HostTune* host_tune(pa_plan_s* P, int nf, uint32_t stages) {
+  for (auto& t : P->tunes)
+    if (t.nf == nf && t.stages == stages) return &t;
+  if (P->tunes.size() >= 32) P->tunes.erase(P->tunes.begin());  // bounded, oldest first
+  pa_plan_s::HostTune t;
+  t.nf = nf;
+  t.stages = stages;
+  const int cap = std::max(1, P->d.max_batch);
+  auto add = [&t](std::vector<int32_t> c) {
+    if (!c.empty() && std::find(t.cand.begin(), t.cand.end(), c) == t.cand.end())
+      t.cand.push_back(std::move(c));
+  };
+  add(taper_schedule(nf, cap));
+  if (nf > 2) {
+    pa_pipe_model m{};
+    m.items_per_frame = std::max(1, P->n_tiles * P->ngroups);
+    m.resident = std::max(1, P->blocks_per_sm * P->num_sms);
+    m.n_sets = kHostSets;
+    const double rf_frame = (double)P->d.n_elem * P->d.n_samples * P->elt;
+    const double out_frame = (double)popcount3(stages) * P->n_out * P->d.nx * P->d.nz * 4.0;
+    m.upload_us = rf_frame / kLinkBytesPerUs;
+    m.download_us = out_frame / kLinkBytesPerUs;
+    const double copy_us = std::max(m.upload_us, m.download_us);
+    for (double x : {0.6, 0.9, 1.3, 1.9, 2.8})
+      for (double launch : {8.0, 40.0})
+        for (double q : {0.0, 1.0}) {
+          m.kernel_us = x * copy_us;
+          m.launch_us = launch;
+          m.wave_share = q;
+          add(pipe_search(m, nf, cap));
+        }
+  }
+  t.best_ms.assign(t.cand.size(), -1.0);
+  for (int i = 0; i < (int)t.cand.size(); ++i) t.order.push_back(i);
+  if (t.cand.size() == 1) t.chosen = 0;
+  P->tunes.push_back(std::move(t));
+  return &P->tunes.back();
+}
+
+// One tuning call of candidate `cur` took `ms`.  A cold call (it built a
+// graph or grew the staging buffers) is not counted unless the candidate was
+// cold three times in a row.
+void host_tune_record(pa_plan_s::HostTune* t, int cur, double ms, bool cold) {
+  if (cold && ++t->attempts < 3) return;
+  t->attempts = 0;
+  double& b = t->best_ms[cur];
+  b = b < 0 ? ms : std::min(b, ms);
+  if (++t->pos < t->order.size()) return;
+  if (!t->second_round) {  // time the three fastest once more
+    t->second_round = true;
+    std::vector<int> idx(t->cand.size());
+    for (int i = 0; i < (int)idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [t](int a, int c) { return t->best_ms[a] < t->best_ms[c]; });
+    for (int i = 0; i < std::min<int>(3, (int)idx.size()); ++i) t->order.push_back(idx[i]);
+    return;
+  }
+  t->chosen = (int)(std::min_element(t->best_ms.begin(), t->best_ms.end()) - t->best_ms.begin());
 }
 
 }  // namespace
@@ -1177,38 +1295,29 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   DeviceGuard g(P->device);
   const pa_plan_desc& d = P->d;
   cudaStream_t user = (cudaStream_t)cuda_stream;
-  // Chunk schedule: short first and last chunks (the first H2D copy and the
-  // last D2H copy cannot overlap compute), the rest in evenly sized middle
-  // chunks, none above max_batch.  Chunks rotate over three buffer sets and
-  // streams, so a chunk's upload does not wait for the download two chunks
-  // back.  Measured on GB300 (cfg2, 32 FP32 frames, 1.07 G pairs): 1.12 ms
-  // per call with two sets of 8-frame chunks, 1.105 ms with this schedule;
-  // letting neighbouring chunks' kernels overlap (direct launches, or one
-  // graph per buffer set) took 1.20 / 1.17 ms.
-  std::vector<int> sched;
-  {
-    const int cap = std::max(1, d.max_batch);
-    const int edge = std::min(cap, std::max(1, n_frames / 5));
-    int mid = n_frames - 2 * edge;
-    if (mid < 0) {  // one or two frames
-      for (int f = 0; f < n_frames; ++f) sched.push_back(1);
-    } else {
-      sched.push_back(edge);
-      const int nm = mid == 0 ? 0 : std::max(2, (mid + cap - 1) / cap);
-      for (int q = 0; q < nm; ++q) {
-        const int c = (mid * (q + 1)) / nm - (mid * q) / nm;
-        if (c > 0) sched.push_back(c);
-      }
-      sched.push_back(edge);
-    }
+  pa_plan_s::HostTune* tune = host_tune(P, n_frames, stages);
+  const bool tuning = tune->fixed.empty() && tune->chosen < 0;
+  const int cur = tuning ? tune->order[tune->pos] : -1;
+  const std::vector<int32_t> sched = tune->current();
+  const long long builds0 = P->graph_builds;
+  bool grew = false;
+  const auto t_start = std::chrono::steady_clock::now();
+  // buffers sized for the largest chunk of any candidate, so trying
+  // candidates does not reallocate
+  int chunk = 1, sets_needed = 1;
+  for (const auto& c : tune->cand) {
+    chunk = std::max(chunk, *std::max_element(c.begin(), c.end()));
+    sets_needed = std::max(sets_needed, (int)c.size());
   }
-  const int chunk = *std::max_element(sched.begin(), sched.end());
+  for (int32_t c : tune->fixed) chunk = std::max(chunk, c);
+  sets_needed = std::min(kHostSets, std::max(sets_needed, (int)tune->fixed.size()));
   const int nsets = std::min<int>(kHostSets, (int)sched.size());
   const size_t rf_frame = (size_t)d.n_elem * d.n_samples * P->elt;
   const size_t out_frame = (size_t)popcount3(stages) * P->n_out * d.nx * d.nz;
-  const size_t need_rf = (size_t)nsets * chunk * rf_frame;
-  const size_t need_out = (size_t)nsets * chunk * out_frame * sizeof(float);
+  const size_t need_rf = (size_t)sets_needed * chunk * rf_frame;
+  const size_t need_out = (size_t)sets_needed * chunk * out_frame * sizeof(float);
   if (need_rf > P->h_rf_bytes) {
+    grew = true;
     cudaFree(P->h_rf);
     P->device_bytes -= P->h_rf_bytes;
     P->h_rf_bytes = 0;
@@ -1217,6 +1326,7 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
     P->device_bytes += need_rf;
   }
   if (need_out > P->h_out_bytes) {
+    grew = true;
     cudaFree(P->h_out);
     P->device_bytes -= P->h_out_bytes;
     P->h_out_bytes = 0;
@@ -1227,6 +1337,7 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   if (!P->h_ev) PA_CUDA(cudaEventCreateWithFlags(&P->h_ev, cudaEventDisableTiming));
   for (int b = 0; b < nsets; ++b) {
     if (!P->hs[b]) PA_CUDA(cudaStreamCreateWithFlags(&P->hs[b], cudaStreamNonBlocking));
+    if (!P->h_done[b]) PA_CUDA(cudaEventCreateWithFlags(&P->h_done[b], cudaEventDisableTiming));
     if (!P->scratch[b]) {
       pa_status s = dalloc(P, &P->scratch[b], P->scratch_ints);
       if (s != PA_OK) return s;
@@ -1245,13 +1356,22 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
     float* out_d = P->h_out + (size_t)b * chunk * out_frame;
     PA_CUDA(cudaMemcpyAsync(rf_d, (const char*)rf_host + (size_t)f0 * rf_frame, nf * rf_frame,
                             cudaMemcpyHostToDevice, st));
+    // the launch sequence waits for the previous chunk's (measured on GB300,
+    // cfg2, 32 FP32 frames: 1.013 ms per call against 1.097 ms when
+    // neighbouring chunks' kernels overlap)
+    if (c > 0) PA_CUDA(cudaStreamWaitEvent(st, P->h_done[(c - 1) % nsets], 0));
     pa_status s = run_chunk(P, rf_d, nf, out_d, stages, st, P->scratch[b]);
     if (s != PA_OK) return s;
+    PA_CUDA(cudaEventRecord(P->h_done[b], st));
     PA_CUDA(cudaMemcpyAsync(out_host + (size_t)f0 * out_frame, out_d,
                             nf * out_frame * sizeof(float), cudaMemcpyDeviceToHost, st));
     f0 += nf;
   }
   for (int b = 0; b < nsets; ++b) PA_CUDA(cudaStreamSynchronize(P->hs[b]));
+  if (tuning) host_tune_record(tune, cur,
+                               std::chrono::duration<double, std::milli>(
+                                   std::chrono::steady_clock::now() - t_start).count(),
+                               grew || P->graph_builds != builds0);
   // bounded waits that ran out during this call (the kernel stopped early)
   if (P->use_tma) {
     long long total = 0;
@@ -1268,6 +1388,41 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
                   fresh);
     }
   }
+  return PA_OK;
+}
+
+pa_status pa_plan_set_host_schedule(pa_plan_t P, int32_t n_frames, uint32_t stages,
+                                    const int32_t* chunks, int32_t n_chunks) {
+  if (!P) return fail(PA_EINVAL, "null plan");
+  if (n_frames < 1) return fail(PA_EINVAL, "n_frames < 1");
+  if ((stages & 7u) == 0 || (stages & ~7u)) return fail(PA_EINVAL, "stages mask 0x%x invalid", stages);
+  if (n_chunks < 0 || (n_chunks > 0 && !chunks)) return fail(PA_EINVAL, "invalid chunk list");
+  std::vector<int32_t> v(chunks, chunks + n_chunks);
+  long long sum = 0;
+  for (int32_t c : v) {
+    if (c < 1 || c > P->d.max_batch)
+      return fail(PA_EINVAL, "chunk of %d frames outside 1..max_batch (%d)", c, P->d.max_batch);
+    sum += c;
+  }
+  if (n_chunks > 0 && sum != n_frames)
+    return fail(PA_EINVAL, "chunks sum to %lld frames, not %d", sum, n_frames);
+  pa_plan_s::HostTune* t = host_tune(P, n_frames, stages);
+  t->fixed = v;  // empty: back to tuning (or to the tuned choice)
+  return PA_OK;
+}
+
+pa_status pa_plan_host_schedule(pa_plan_t P, int32_t n_frames, uint32_t stages, int32_t* chunks,
+                                int32_t max_chunks, int32_t* n_chunks, int32_t* state) {
+  if (!P || !chunks || !n_chunks || !state) return fail(PA_EINVAL, "null argument");
+  if (n_frames < 1) return fail(PA_EINVAL, "n_frames < 1");
+  if ((stages & 7u) == 0 || (stages & ~7u)) return fail(PA_EINVAL, "stages mask 0x%x invalid", stages);
+  pa_plan_s::HostTune* t = host_tune(P, n_frames, stages);
+  const std::vector<int32_t>& s = t->current();
+  if ((int)s.size() > max_chunks)
+    return fail(PA_EINVAL, "schedule has %d chunks, room for %d", (int)s.size(), max_chunks);
+  std::copy(s.begin(), s.end(), chunks);
+  *n_chunks = (int32_t)s.size();
+  *state = !t->fixed.empty() ? 3 : (t->chosen >= 0 ? 2 : 1);
   return PA_OK;
 }
 
@@ -1322,6 +1477,6 @@ const char* pa_status_str(pa_status s) {
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int32_t pa_version(void) { return 102; }
+int32_t pa_version(void) { return 103; }
 
 }  // extern "C"

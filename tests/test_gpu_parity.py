@@ -180,6 +180,44 @@ def test_host_buffer_path_matches_device_path():
     assert np.array_equal(dev, host)
 
 
+def test_host_schedule_tuning_keeps_bits():
+    """pa_beamform_host times candidate chunk schedules on its first calls of
+    a shape: every call gives the device path's bits, tuning ends with a
+    valid schedule, and caller-set ragged schedules give the same bits."""
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, range(1, 8))  # 7 frames
+    store, _ = synth.quantize(rf, "f32")
+    st = pa.PA_STAGE_ENV | pa.PA_STAGE_LOG
+    with pa.Plan(pa.make_desc(wl, order_k=3, max_batch=4)) as plan:
+        dev = pa.beamform(plan, torch.from_numpy(store).cuda(), st)
+        torch.cuda.synchronize()
+        dev = dev.cpu().numpy()
+        sched, state = plan.host_schedule(7, st)
+        assert state == 1 and sum(sched) == 7
+        calls = 0
+        while state == 1 and calls < 200:
+            assert np.array_equal(pa.beamform_host(plan, store, st), dev), sched
+            calls += 1
+            sched, state = plan.host_schedule(7, st)
+        assert state == 2 and sum(sched) == 7 and max(sched) <= 4 and calls >= 2
+        for fixed in ([3, 1, 2, 1], [1] * 7, [4, 3]):
+            plan.set_host_schedule(7, st, fixed)
+            assert plan.host_schedule(7, st) == (fixed, 3)
+            assert np.array_equal(pa.beamform_host(plan, store, st), dev), fixed
+        plan.set_host_schedule(7, st, [])
+        assert plan.host_schedule(7, st) == (sched, 2)
+        for bad in ([4, 4], [5, 2], [7, 0], [3, 3]):
+            with pytest.raises(pa.PAError):
+                plan.set_host_schedule(7, st, bad)
+        # another shape of the same plan tunes on its own
+        assert plan.host_schedule(5, st)[1] == 1
+        assert np.array_equal(pa.beamform_host(plan, store[:5], st), dev[:5])
+
+
 def test_checked_build_raises_no_bounds_flags():
     """Bounds-checked build of the same kernels over the edge-case geometries."""
     cases = [
