@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "pa_internal.cuh"
+#include "pa_logdb.cuh"
 
 namespace {
 
@@ -47,10 +48,7 @@ __global__ void k_noalloc_log(const float* env, float* out, long long elems, con
   float* dst = out + (size_t)img * elems;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < elems;
        q += (long long)gridDim.x * blockDim.x) {
-    const float e = src[q];
-    float v = -dr;
-    if (mx > 0.f && e > 0.f) v = fminf(0.f, fmaxf(-dr, 20.0f * log10f(e * inv)));
-    dst[q] = v;
+    dst[q] = pa::log_db(src[q], mx, inv, dr);
   }
 }
 

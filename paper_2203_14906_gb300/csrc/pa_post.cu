@@ -18,6 +18,7 @@
 //
 // k_log: 20 log10(env / image max), clipped to [-DR, 0]; elementwise.
 #include "pa_internal.cuh"
+#include "pa_logdb.cuh"
 
 namespace pa {
 
@@ -573,9 +574,6 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
   if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
 }
 
-__device__ __forceinline__ float log_db(float env, float mx, float inv, float dr) {
-  return (mx > 0.f && env > 0.f) ? fminf(0.f, fmaxf(-dr, 20.0f * log10f(env * inv))) : -dr;
-}
 
 __global__ void __launch_bounds__(256) k_log(const LogParams p) {
   const int img = blockIdx.y;  // frame * n_out + output

@@ -47,6 +47,7 @@ def test_noalloc_log_matches_plan_log_two_calls():
         torch.cuda.synchronize()
         diff = float((got - want).abs().max().item())
         assert diff <= TOL_DB, f"call {call}: max |dB| difference {diff}"
+        assert torch.equal(got, want), "same log function, same bits"
         assert float(got.max().item()) == 0.0 and float(got.min().item()) >= -60.0
 
 
