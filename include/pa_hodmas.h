@@ -178,7 +178,11 @@ pa_status pa_beamform(pa_plan_t plan, const void* rf_dev, int32_t n_frames,
  * streams; the launch sequence of a chunk starts after the previous chunk's
  * (neighbouring launches do not share the GPU), while uploads and downloads
  * overlap them.  The chunk schedule per (n_frames, stages) is tuned over the
- * first calls of that shape (pa_plan_host_schedule).
+ * first calls of that shape (pa_plan_host_schedule).  With both host buffers
+ * pinned (and graph launch enabled, kernel timing off) the whole call is one
+ * CUDA graph launched on cuda_stream: the plan keeps one per (n_frames,
+ * stages, schedule), at most 64, and rewrites only its host addresses when
+ * the caller's buffers change.
  * Errors: as pa_beamform, plus PA_ETIMEOUT when a thread block of the fused
  * kernel gave up waiting for its TMA staging copies (a bounded wait of about
  * a second; the block stops early, so the output is incomplete;

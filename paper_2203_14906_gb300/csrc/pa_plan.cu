@@ -123,6 +123,22 @@ struct pa_plan_s {
   };
   std::vector<HostTune> tunes;
   long long graph_builds = 0;  // executable graphs instantiated so far
+  // whole host-path calls as graphs (pinned host buffers): every chunk's
+  // upload, launch sequence and download, per (frames, stages, schedule);
+  // they name the staging buffers, so growing those drops them
+  struct HostGraph {
+    int nf = 0;
+    uint32_t stages = 0;
+    std::vector<int32_t> sched;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> up, down;  // per chunk
+    std::vector<void*> up_dev, down_dev;
+    std::vector<size_t> up_off, down_off, up_bytes, down_bytes;
+    const void* rf_host = nullptr;
+    float* out_host = nullptr;
+  };
+  std::vector<HostGraph> host_graphs;
   // CUDA graphs of the launch sequence, one per (frames, stages)
   struct GraphEntry {
     int nf = 0;
@@ -518,6 +534,10 @@ void free_plan(pa_plan_s* P) {
   for (int s = 0; s < kHostSets; ++s)
     if (P->h_done[s]) cudaEventDestroy(P->h_done[s]);
   for (auto& g : P->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
+  for (auto& g : P->host_graphs) {
     cudaGraphExecDestroy(g.exec);
     cudaGraphDestroy(g.graph);
   }
@@ -1138,6 +1158,145 @@ void host_tune_record(pa_plan_s::HostTune* t, int cur, double ms, bool cold) {
   t->chosen = (int)(std::min_element(t->best_ms.begin(), t->best_ms.end()) - t->best_ms.begin());
 }
 
+void drop_host_graphs(pa_plan_s* P) {
+  for (auto& g : P->host_graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
+  P->host_graphs.clear();
+}
+
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// The graph of one host-path call: per chunk c (buffer set b = c mod sets)
+// an upload, the launch sequence (clear, fused kernel, post, log) and a
+// download, with the ordering of the stream form: a launch sequence after
+// its upload and after the previous chunk's launch sequence, a download
+// after its launch sequence, an upload into set b after the download that
+// last used set b.
+pa_status build_host_graph(pa_plan_s* P, pa_plan_s::HostGraph& hg, const void* rf_host,
+                           float* out_host, int chunk, int nsets) {
+  const pa_plan_desc& d = P->d;
+  const size_t rf_frame = (size_t)d.n_elem * d.n_samples * P->elt;
+  const size_t out_frame = (size_t)popcount3(hg.stages) * P->n_out * d.nx * d.nz;
+  cudaGraph_t graph;
+  PA_CUDA(cudaGraphCreate(&graph, 0));
+  cudaError_t e = cudaSuccess;
+  cudaGraphNode_t prev_last = nullptr;
+  int f0 = 0;
+  for (size_t c = 0; c < hg.sched.size() && e == cudaSuccess; ++c) {
+    const int nf = hg.sched[c];
+    const int b = (int)(c % nsets);
+    char* rf_d = (char*)P->h_rf + (size_t)b * chunk * rf_frame;
+    float* out_d = P->h_out + (size_t)b * chunk * out_frame;
+    const size_t up_off = (size_t)f0 * rf_frame, up_bytes = nf * rf_frame;  // bytes
+    const size_t down_off = (size_t)f0 * out_frame;                          // floats
+    const size_t down_bytes = nf * out_frame * sizeof(float);
+    cudaGraphNode_t up = nullptr, down = nullptr;
+    {
+      cudaGraphNode_t dep = c >= (size_t)nsets ? hg.down[c - nsets] : nullptr;
+      e = cudaGraphAddMemcpyNode1D(&up, graph, dep ? &dep : nullptr, dep ? 1 : 0, rf_d,
+                                   (const char*)rf_host + up_off, up_bytes, cudaMemcpyHostToDevice);
+    }
+    ChunkLaunch cl;
+    if (e == cudaSuccess) {
+      const pa_status ps = prepare_chunk(P, rf_d, nf, out_d, hg.stages, P->scratch[b], &cl);
+      if (ps != PA_OK) {
+        cudaGraphDestroy(graph);
+        return ps;
+      }
+    }
+    cudaGraphNode_t last = nullptr;
+    if (e == cudaSuccess) {
+      void* ab[] = {&cl.b};
+      void* aq[] = {&cl.q};
+      void* al[] = {&cl.l};
+      int zn = (int)cl.zero_ints;
+      void* az[] = {&cl.zero, &zn};
+      LaunchSpec sz;
+      sz.func = reinterpret_cast<const void*>(k_zero_ints);
+      sz.grid = dim3(1);
+      sz.block = dim3(256);
+      const cudaKernelNodeParams kz = node_params(sz, az);
+      const cudaKernelNodeParams kb = node_params(cl.sb, ab);
+      cudaGraphNode_t deps[2] = {up, prev_last};
+      cudaGraphNode_t nz = nullptr, nb = nullptr;
+      e = cudaGraphAddKernelNode(&nz, graph, deps, prev_last ? 2 : 1, &kz);
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nb, graph, &nz, 1, &kb);
+      last = nb;
+      if (e == cudaSuccess && cl.post) {
+        const cudaKernelNodeParams kq = node_params(cl.sq, aq);
+        cudaGraphNode_t nq = nullptr;
+        e = cudaGraphAddKernelNode(&nq, graph, &last, 1, &kq);
+        last = nq;
+      }
+      if (e == cudaSuccess && cl.log) {
+        const cudaKernelNodeParams kl = node_params(cl.sl, al);
+        cudaGraphNode_t nl = nullptr;
+        e = cudaGraphAddKernelNode(&nl, graph, &last, 1, &kl);
+        last = nl;
+      }
+    }
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&down, graph, &last, 1, out_host + down_off, out_d, down_bytes,
+                                   cudaMemcpyDeviceToHost);
+    hg.up.push_back(up);
+    hg.down.push_back(down);
+    hg.up_dev.push_back(rf_d);
+    hg.down_dev.push_back(out_d);
+    hg.up_off.push_back(up_off);
+    hg.down_off.push_back(down_off);
+    hg.up_bytes.push_back(up_bytes);
+    hg.down_bytes.push_back(down_bytes);
+    prev_last = last;
+    f0 += nf;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&hg.exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(PA_ECUDA, "host-path graph build: %s", cudaGetErrorString(e));
+  }
+  hg.graph = graph;
+  hg.rf_host = rf_host;
+  hg.out_host = out_host;
+  ++P->graph_builds;
+  return PA_OK;
+}
+
+// End of a host-path call: the tuning record, then the bounded waits that
+// ran out during the call (the kernel stopped early).
+pa_status host_call_done(pa_plan_s* P, pa_plan_s::HostTune* tune, bool tuning, int cur,
+                         std::chrono::steady_clock::time_point t_start, bool cold) {
+  if (tuning)
+    host_tune_record(tune, cur,
+                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                               t_start).count(),
+                     cold);
+  if (P->use_tma) {
+    long long total = 0;
+    for (int b = 0; b < kHostSets; ++b) {
+      if (!P->scratch[b]) continue;
+      int n = 0;
+      PA_CUDA(cudaMemcpy(&n, P->scratch[b] + P->scratch_ints - 1, sizeof n, cudaMemcpyDeviceToHost));
+      total += n;
+    }
+    if (total > P->timeouts_seen) {
+      const long long fresh = total - P->timeouts_seen;
+      P->timeouts_seen = total;
+      return fail(PA_ETIMEOUT, "%lld thread block(s) gave up waiting for their RF staging copies",
+                  fresh);
+    }
+  }
+  return PA_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ dispatchers
@@ -1318,6 +1477,7 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   const size_t need_out = (size_t)sets_needed * chunk * out_frame * sizeof(float);
   if (need_rf > P->h_rf_bytes) {
     grew = true;
+    drop_host_graphs(P);
     cudaFree(P->h_rf);
     P->device_bytes -= P->h_rf_bytes;
     P->h_rf_bytes = 0;
@@ -1327,6 +1487,7 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
   }
   if (need_out > P->h_out_bytes) {
     grew = true;
+    drop_host_graphs(P);
     cudaFree(P->h_out);
     P->device_bytes -= P->h_out_bytes;
     P->h_out_bytes = 0;
@@ -1343,6 +1504,41 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
       if (s != PA_OK) return s;
       PA_CUDA(cudaMemset(P->scratch[b], 0, P->scratch_ints * sizeof(int)));
     }
+  }
+  if (P->use_graph && !P->prof && is_pinned(rf_host) && is_pinned(out_host)) {
+    // pinned buffers: the whole call is one graph launch on the caller's stream
+    pa_plan_s::HostGraph* hg = nullptr;
+    for (auto& g : P->host_graphs)
+      if (g.nf == n_frames && g.stages == stages && g.sched == sched) hg = &g;
+    if (!hg) {
+      if (P->host_graphs.size() >= 64) {  // bounded, oldest first
+        cudaGraphExecDestroy(P->host_graphs.front().exec);
+        cudaGraphDestroy(P->host_graphs.front().graph);
+        P->host_graphs.erase(P->host_graphs.begin());
+      }
+      pa_plan_s::HostGraph g;
+      g.nf = n_frames;
+      g.stages = stages;
+      g.sched = sched;
+      pa_status s = build_host_graph(P, g, rf_host, out_host, chunk, nsets);
+      if (s != PA_OK) return s;
+      P->host_graphs.push_back(std::move(g));
+      hg = &P->host_graphs.back();
+    } else if (hg->rf_host != rf_host || hg->out_host != out_host) {
+      for (size_t c = 0; c < hg->sched.size(); ++c) {
+        PA_CUDA(cudaGraphExecMemcpyNodeSetParams1D(hg->exec, hg->up[c], hg->up_dev[c],
+                                                   (const char*)rf_host + hg->up_off[c],
+                                                   hg->up_bytes[c], cudaMemcpyHostToDevice));
+        PA_CUDA(cudaGraphExecMemcpyNodeSetParams1D(hg->exec, hg->down[c],
+                                                   out_host + hg->down_off[c], hg->down_dev[c],
+                                                   hg->down_bytes[c], cudaMemcpyDeviceToHost));
+      }
+      hg->rf_host = rf_host;
+      hg->out_host = out_host;
+    }
+    PA_CUDA(cudaGraphLaunch(hg->exec, user));
+    PA_CUDA(cudaStreamSynchronize(user));
+    return host_call_done(P, tune, tuning, cur, t_start, grew || P->graph_builds != builds0);
   }
   // the internal streams start after work already queued on the caller's stream
   PA_CUDA(cudaEventRecord(P->h_ev, user));
@@ -1368,28 +1564,9 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
     f0 += nf;
   }
   for (int b = 0; b < nsets; ++b) PA_CUDA(cudaStreamSynchronize(P->hs[b]));
-  if (tuning) host_tune_record(tune, cur,
-                               std::chrono::duration<double, std::milli>(
-                                   std::chrono::steady_clock::now() - t_start).count(),
-                               grew || P->graph_builds != builds0);
-  // bounded waits that ran out during this call (the kernel stopped early)
-  if (P->use_tma) {
-    long long total = 0;
-    for (int b = 0; b < kHostSets; ++b) {
-      if (!P->scratch[b]) continue;
-      int n = 0;
-      PA_CUDA(cudaMemcpy(&n, P->scratch[b] + P->scratch_ints - 1, sizeof n, cudaMemcpyDeviceToHost));
-      total += n;
-    }
-    if (total > P->timeouts_seen) {
-      const long long fresh = total - P->timeouts_seen;
-      P->timeouts_seen = total;
-      return fail(PA_ETIMEOUT, "%lld thread block(s) gave up waiting for their RF staging copies",
-                  fresh);
-    }
-  }
-  return PA_OK;
+  return host_call_done(P, tune, tuning, cur, t_start, grew || P->graph_builds != builds0);
 }
+
 
 pa_status pa_plan_set_host_schedule(pa_plan_t P, int32_t n_frames, uint32_t stages,
                                     const int32_t* chunks, int32_t n_chunks) {

@@ -218,6 +218,35 @@ def test_host_schedule_tuning_keeps_bits():
         assert np.array_equal(pa.beamform_host(plan, store[:5], st), dev[:5])
 
 
+def test_host_call_graph_with_pinned_buffers():
+    """Pinned host buffers run the whole host-path call as one graph (per
+    frames, stages and schedule; rebuilt while the schedule is tuned, host
+    addresses rewritten when the caller's buffers change); pageable buffers
+    take the stream form.  Every call gives the device path's bits."""
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, range(1, 10))  # 9 frames
+    store, _ = synth.quantize(rf, "f32")
+    st = pa.PA_STAGE_ENV | pa.PA_STAGE_LOG
+    with pa.Plan(pa.make_desc(wl, order_k=4, max_batch=4)) as plan:
+        dev = pa.beamform(plan, torch.from_numpy(store).cuda(), st)
+        torch.cuda.synchronize()
+        dev = dev.cpu().numpy()
+        rf_p = torch.from_numpy(store).pin_memory()
+        outs = [torch.empty(plan.out_shape(9, st), dtype=torch.float32).pin_memory()
+                for _ in range(2)]
+        for call in range(60):
+            out = outs[call % 2] if call % 7 else None  # None: a pageable result array
+            got = pa.beamform_host(plan, rf_p if call % 5 else store, st, out=out)
+            got = got.numpy() if isinstance(got, torch.Tensor) else got
+            assert np.array_equal(got, dev), call
+        assert plan.host_schedule(9, st)[1] == 2
+        assert plan.info()["device_error_flags"] == 0
+
+
 def test_checked_build_raises_no_bounds_flags():
     """Bounds-checked build of the same kernels over the edge-case geometries."""
     cases = [
