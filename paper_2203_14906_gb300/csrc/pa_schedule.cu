@@ -66,8 +66,9 @@ double pipe_makespan(const pa_pipe_model& m, const int32_t* ch, int n) {
 }
 
 // Search over head a, middle chunk size mid, first tail chunk t1 and tail
-// ratio rho (and the single chunk).  Middle chunks are limited to 256 per
-// schedule.
+// ratio rho (and the single chunk).  Middle sizes that would need more than
+// 256 middle chunks are skipped, except chunks of cap frames, so the cost
+// stays bounded for long calls.
 std::vector<int32_t> pipe_search(const pa_pipe_model& m, int n, int cap) {
   std::vector<int32_t> best, ch;
   if (n <= 0) return best;
@@ -93,7 +94,7 @@ std::vector<int32_t> pipe_search(const pa_pipe_model& m, int n, int cap) {
         if (rest < 0) continue;
         for (int mid = 1; mid <= cap; ++mid) {
           if (rest == 0 && mid > 1) break;
-          if (rest / mid > 256) continue;
+          if (rest / mid > 256 && mid != cap) continue;  // long calls: full chunks only
           ch.clear();
           ch.push_back(a);
           if (rest % mid) ch.push_back(rest % mid);

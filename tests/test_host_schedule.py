@@ -102,3 +102,17 @@ def test_invalid_models_and_schedules():
         pa.pipe_schedule(0, 4, **model())
     with pytest.raises(pa.PAError):
         pa.pipe_schedule(4, 0, **model())
+
+
+def test_long_calls_get_full_middle_chunks():
+    """10 000 frames in chunks of at most 32: the search stays quick and
+    returns a valid schedule built from full middle chunks."""
+    import time
+
+    m = model(items_per_frame=256, resident=608, upload_us=4.9, download_us=16.4,
+              kernel_us=25.0, launch_us=30.0, wave_share=0.5)
+    t0 = time.perf_counter()
+    s = pa.pipe_schedule(10000, 32, **m)
+    assert time.perf_counter() - t0 < 5.0
+    _valid(s, 10000, 32)
+    assert s.count(32) >= 300
