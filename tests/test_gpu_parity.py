@@ -247,6 +247,45 @@ def test_host_call_graph_with_pinned_buffers():
         assert plan.info()["device_error_flags"] == 0
 
 
+def _random_workload(rng, case):
+    m = int(rng.integers(1, 5))
+    n_elem = int(rng.integers(8, 72))
+    dx = 0.3e-3 / m
+    nx = int(rng.integers(9, 110))
+    nz = int(rng.integers(17, 160))
+    dz = float(rng.uniform(40e-6, 110e-6))
+    x0 = -nx * dx / 2 + float(rng.uniform(-1.0, 1.0)) * 2e-3
+    z0 = float(rng.uniform(0.0, 4e-3))
+    wl = synth.workload(
+        "cfg1", n_elem=n_elem, nx=nx, nz=nz, x0_m=x0, x1_m=x0 + nx * dx, z0_m=z0,
+        z1_m=z0 + nz * dz, n_samples=int(rng.integers(300, 1400)),
+        t0_s=float(rng.choice([0.0, 0.5e-6])), n_points=3,
+        f_number=1.5 if case % 4 == 3 else 0.0,
+        interp="nearest" if case % 3 == 2 else "linear")
+    wl["seeds"] = [int(rng.integers(1, 1000))]
+    return wl
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_random_geometries(case):
+    """Seeded random geometries: lattice factor 1-4, 8-71 channels, ragged
+    grids (9-109 x 17-159), record lengths not divisible by 4, off-centre
+    windows, time offsets, F-number apodisation, nearest-sample delays, every
+    RF type and orders 1-8; every stage against the oracle on the same
+    (dequantised) RF at the FP32 tolerance."""
+    rng = np.random.default_rng(1000 + case)
+    wl = _random_workload(rng, case)
+    k = int(rng.integers(1, 9))
+    dtype = str(rng.choice(["f32", "bf16", "f16"]))
+    rf = _frames(wl, [wl["seeds"][0], wl["seeds"][0] + 1])
+    out, info, deq = run_gpu(wl, rf, k, rf_dtype=dtype, compensated=int(dtype != "f32"),
+                             max_batch=int(rng.integers(1, 3)))
+    assert info["device_error_flags"] == 0
+    what = (f"case {case}: N={wl['n_elem']} m={info['lattice_m']} grid={wl['nx']}x{wl['nz']} "
+            f"Ns={wl['n_samples']} k={k} {dtype} F#={wl['f_number']} {wl['interp']}")
+    assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=what)
+
+
 def test_checked_build_raises_no_bounds_flags():
     """Bounds-checked build of the same kernels over the edge-case geometries."""
     cases = [
