@@ -138,9 +138,10 @@ typedef struct {
  * non-integer pitch / dx), PA_EUNSUPPORTED (lattice m > 32, RF window too
  * large for shared memory), PA_ENOMEM, PA_ECUDA.
  * Environment, read here (for measurements and tests; results do not depend
- * on the first two): PA_STAGING=tma|loads picks the RF staging path (TMA
+ * on the first three): PA_STAGING=tma|loads picks the RF staging path (TMA
  * boxes need Ns to be a multiple of the window alignment), PA_CHUNK_STEPS=n
- * caps the channel steps per staged chunk, PA_INJECT_TMA_SHORTFALL makes
+ * caps the channel steps per staged chunk, PA_LANE_ROWS=32|16|8 sets the
+ * depth rows per lane group of the fused kernel, PA_INJECT_TMA_SHORTFALL makes
  * every TMA chunk expect 16 bytes more than it receives, so each block's
  * bounded wait runs out (failure-detection tests).
  */

@@ -485,11 +485,20 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     if (threadIdx.x == 0) s_item[2] = atomicAdd(p.counter, 1);
     const ItemInfo it = decode_item(p, item);
     const int tz = it.tz, tx = it.tx, tile_id = it.tile_id, grp = it.grp, frame = it.frame;
-    const int sl = grp * nwarps + warp;
+    // Lanes -> (warp slot, depth row): lane_rows consecutive rows of
+    // 32 / lane_rows neighbouring slots per warp; the block's warps cover its
+    // slots x the tile's 32 rows.  Fewer rows per lane group shrink the
+    // span of a half-warp's 64-bit shared gather (the delay advances ~2
+    // samples per row).
+    const int lr_log2 = p.lane_rows_log2;
+    const int spw_log2 = 5 - lr_log2;              // slots per warp
+    const int sg = nwarps >> spw_log2;             // slot groups of the block
+    const int sl = grp * nwarps + ((warp % sg) << spw_log2) + (lane >> lr_log2);
+    const int zr = ((warp / sg) << lr_log2) + (lane & ((1 << lr_log2) - 1));
     const int2 rg = __ldg(p.slot_rg + sl);
     const int r_m = rg.x, g = rg.y;
     const int jt = tx * p.tile_x + g * p.m * kC + r_m;
-    const int z = tz * p.tile_z + lane;
+    const int z = tz * p.tile_z + zr;
     const int2 ur = __ldg(p.urange + (size_t)tile_id * p.slots + sl);
     const int2 vk = __ldg(p.vchunks + (size_t)tile_id * p.ngroups + grp);
 

@@ -57,6 +57,7 @@ struct BfParams {  // aligned as CUtensorMap requires
   int rf_dtype;           // pa_rf_dtype
   int vec_ok;             // rows start 8/16-byte aligned (Ns % 4 == 0)
   int nearest;            // 1: nearest-sample delays (a = 0), one tap per pair
+  int lane_rows_log2;     // log2 of the depth rows per lane group: 5, 4 or 3
   int nc, ncs;            // channel steps per chunk, virtual channels staged per chunk
   int cmp_off;            // shared offset of the compensated totals (compensated sums)
   int n_elem, n_samples;

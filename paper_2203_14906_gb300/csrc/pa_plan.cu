@@ -150,6 +150,7 @@ struct pa_plan_s {
   };
   std::vector<GraphEntry> graphs;
   bool use_graph = true;
+  int lane_rows_log2 = 5;  // depth rows per lane group of the fused kernel (log2)
   // kernel timing (pa_plan_profile)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
@@ -399,6 +400,18 @@ void configure(pa_plan_s* P) {
   }
   P->warps = B;
   P->ngroups = P->slots / B;
+  // Lane groups of 8 rows x 4 neighbouring slots (a half-warp's shared
+  // gather spans ~18 slots instead of ~32) where the block's warps split
+  // that way and there is no apodisation; apodised plans keep 32 rows x 1
+  // slot, because a warp iterates over the union of its slots' channel
+  // ranges.  Measured on GB300: cfg2 FP32 k = 3 0.651 -> 0.642 ms, cfg5
+  // (apodised) 2.91 -> 3.07 ms with 8-row groups; 16-row groups gained
+  // nothing.  PA_LANE_ROWS=32|16|8 picks one, for comparisons.
+  P->lane_rows_log2 = (B % 4 == 0 && !P->apod) ? 3 : 5;
+  if (const char* e = getenv("PA_LANE_ROWS")) {
+    const int want = atoi(e) == 8 ? 3 : (atoi(e) == 16 ? 4 : 5);
+    if (B % (1 << (5 - want)) == 0) P->lane_rows_log2 = want;
+  }
   P->threads = 32 * B;
   P->tile_x = P->m * kC * P->R;
   P->tile_z = 32;
@@ -882,6 +895,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.rf_dtype = (int)d.rf_dtype;
   b.vec_ok = (d.n_samples % 4) == 0;
   b.nearest = d.interp == PA_INTERP_NEAREST;
+  b.lane_rows_log2 = P->lane_rows_log2;
   b.n_elem = d.n_elem;
   b.n_samples = d.n_samples;
   b.frame_elems = (long long)d.n_elem * d.n_samples;

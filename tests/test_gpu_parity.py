@@ -336,6 +336,20 @@ def test_tma_and_load_staging_agree(dtype, monkeypatch):
     assert np.array_equal(outs["tma"], outs["loads"])
 
 
+def test_lane_groups_keep_bits(monkeypatch):
+    """Lane groups of 32, 16 and 8 depth rows (one, two or four slots per
+    warp) give the same bits: each pixel's channel order is unchanged."""
+    for wl, k in ((synth.workload("cfg1"), 3), (synth.workload("cfg1", f_number=1.5), 4)):
+        rf = _frames(wl, [2, 3])
+        outs = []
+        for rows in ("32", "16", "8"):
+            monkeypatch.setenv("PA_LANE_ROWS", rows)
+            out, info, _ = run_gpu(wl, rf, k)
+            assert info["device_error_flags"] == 0
+            outs.append(out)
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
 def test_long_columns_and_odd_width():
     """nz > 1024 (2048-point envelope transforms, the out-of-place FFT path),
     an odd number of columns (the last column pair has one column) and a
