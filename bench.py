@@ -206,7 +206,7 @@ def kernel_source_hash():
 
 # Plan facts that fix the fused kernel's launch (grid, block, shared memory).
 LAUNCH_FIELDS = ("threads", "blocks_per_sm", "window", "chunk_steps", "tile_x", "tile_z",
-                 "tma_staging")
+                 "tma_staging", "lane_rows")
 
 
 def measured_traffic(kind, info=None):

@@ -123,6 +123,9 @@ typedef struct {
                                   device.                                  */
   int32_t chunk_steps;        /* channel steps staged per shared-memory
                                  chunk of the fused kernel                 */
+  int32_t lane_rows;          /* depth rows per lane group of the fused
+                                 kernel (32, 16 or 8; a warp covers
+                                 32 / lane_rows neighbouring slots)        */
 } pa_plan_info;
 
 /*

@@ -110,6 +110,7 @@ class PlanInfo(ctypes.Structure):
         ("tma_staging", ctypes.c_int32),
         ("device_error_flags", ctypes.c_uint32),
         ("chunk_steps", ctypes.c_int32),
+        ("lane_rows", ctypes.c_int32),
     ]
 
     def as_dict(self):

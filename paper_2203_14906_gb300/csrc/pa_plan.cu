@@ -401,13 +401,16 @@ void configure(pa_plan_s* P) {
   P->warps = B;
   P->ngroups = P->slots / B;
   // Lane groups of 8 rows x 4 neighbouring slots (a half-warp's shared
-  // gather spans ~18 slots instead of ~32) where the block's warps split
-  // that way and there is no apodisation; apodised plans keep 32 rows x 1
-  // slot, because a warp iterates over the union of its slots' channel
-  // ranges.  Measured on GB300: cfg2 FP32 k = 3 0.651 -> 0.642 ms, cfg5
-  // (apodised) 2.91 -> 3.07 ms with 8-row groups; 16-row groups gained
-  // nothing.  PA_LANE_ROWS=32|16|8 picks one, for comparisons.
-  P->lane_rows_log2 = (B % 4 == 0 && !P->apod) ? 3 : 5;
+  // gather spans ~18 slots instead of ~32) for orders <= 4 without
+  // apodisation, where the block's warps split that way.  Apodised plans
+  // keep 32 rows x 1 slot, because a warp iterates over the union of its
+  // slots' channel ranges; orders >= 5 are arithmetic-bound and lose to the
+  // split table loads of 8-row groups.  Measured on GB300 (fused kernel per
+  // launch, 32 -> 8 rows): cfg2 FP32 k = 1, 2 0.594 -> 0.488 ms, k = 3
+  // 0.651 -> 0.641 ms, k = 4 0.701 -> 0.692 ms, k = 5 0.831 -> 0.837 ms,
+  // k = 7 1.280 -> 1.339 ms; cfg5 (apodised) 2.91 -> 3.06 ms; 16-row groups
+  // were never the fastest.  PA_LANE_ROWS=32|16|8 picks one, for comparisons.
+  P->lane_rows_log2 = (B % 4 == 0 && !P->apod && P->K <= 4) ? 3 : 5;
   if (const char* e = getenv("PA_LANE_ROWS")) {
     const int want = atoi(e) == 8 ? 3 : (atoi(e) == 16 ? 4 : 5);
     if (B % (1 << (5 - want)) == 0) P->lane_rows_log2 = want;
@@ -1421,6 +1424,7 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->device_bytes = P->device_bytes;
   info->tma_staging = P->use_tma ? 1 : 0;
   info->chunk_steps = P->nc;
+  info->lane_rows = 1 << P->lane_rows_log2;
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);
