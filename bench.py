@@ -50,7 +50,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--form", default="fp32", choices=["fp32", "precision"],
+                    help="arithmetic form of the headline leg: FP32 RF and plain sums, or BF16 "
+                         "RF with Kahan-compensated sums")
     return ap.parse_args()
+
+
+def form_dtype(args):
+    """(RF storage type, compensated) of the headline leg."""
+    return ("bf16", 1) if args.form == "precision" else ("f32", 0)
 
 
 def workload():
@@ -64,7 +72,8 @@ def config_dict(args, wl, extra=None):
         "workload": (
             f"cfg2 geometry: {wl['n_elem']} el x {wl['n_samples']} samples @ {wl['fs_hz']/1e6:g} MHz, "
             f"{wl['nx']}x{wl['nz']} grid; DAS+DMAS+DMAS-{args.order} in one pass; band-pass, "
-            "Hilbert envelope, log; FP32 RF"
+            "Hilbert envelope, log; "
+            + ("BF16 RF, Kahan-compensated sums" if args.form == "precision" else "FP32 RF")
         ),
         "frames_per_step": args.frames,
         "order_k": args.order,
@@ -595,7 +604,8 @@ def run_ours(args):
     barrier()
     clk = ClockSampler(local)
     clk.start()
-    times, prof, info = time_form(pa, torch, wl, args, "f32", 0, frames64, stream, flush)
+    rf_dtype, comp = form_dtype(args)
+    times, prof, info = time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush)
     clocks = clk.stop()
     barrier()
     t_tot = max_over_ranks(sum(times), pg, dev)
@@ -623,9 +633,12 @@ def run_ours(args):
     launches = int(sum(v[1] for v in prof.values()) + prof["bf_fused"][1])
 
     # ---- end to end through the host-buffer ABI call
-    desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype="f32", max_batch=F)
-    store, _ = synth.quantize(frames64, "f32")
-    rf_h = torch.from_numpy(store).pin_memory()
+    desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype=rf_dtype, max_batch=F, compensated=comp)
+    store, _ = synth.quantize(frames64, rf_dtype)
+    if rf_dtype == "bf16":
+        rf_h = torch.from_numpy(store.view(np.int16)).view(torch.bfloat16).pin_memory()
+    else:
+        rf_h = torch.from_numpy(store).pin_memory()
     with pa.Plan(desc) as plan:
         out_h = torch.empty(plan.out_shape(F, pa.PA_STAGE_LOG), dtype=torch.float32).pin_memory()
         for _ in range(max(1, args.warmup)):

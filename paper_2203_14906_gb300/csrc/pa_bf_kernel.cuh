@@ -380,71 +380,97 @@ __device__ __forceinline__ ItemInfo decode_item(const BfParams& p, int item) {
   return it;
 }
 
-// Kahan fold of the partial sums into the running totals, held in registers
-// (orders <= 3: the plain kernel's register budget is the limit anyway).
-template <int NA>
-__device__ __forceinline__ void kahan_fold(float (&acc)[kC][NA], float (&tot)[kC][NA],
-                                           float (&cmp)[kC][NA]) {
+// ---- Tensor memory (TMEM) for the compensated totals of orders <= 3 -------
+// The kernel does no matrix work, so the SM's 256 KB of tensor memory is
+// free to hold the Kahan totals and compensation terms.  Warp w reaches TMEM
+// lanes 32 (w % 4) .. 32 (w % 4) + 31 (lane = its own lane); warps w and
+// w + 4 share those lanes and split the columns.  Accumulator q of a thread
+// lives in 8 consecutive 32-bit columns: the totals of its kC = 4 pixels,
+// then their compensation terms.  Every load and store waits for its own
+// completion inside the same asm statement, so no TMEM access is in flight
+// once a thread passes a barrier.
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, int ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(dst_smem), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
-  for (int c = 0; c < kC; ++c) {
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      const float y = acc[c][q] - cmp[c][q];
-      const float t = tot[c][q] + y;
-      cmp[c][q] = (t - tot[c][q]) - y;
-      tot[c][q] = t;
-      acc[c][q] = 0.f;
-    }
-  }
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
 }
 
-// The same fold with totals and compensation terms in shared memory (float4
-// q of thread t holds accumulator q of the thread's kC = 4 columns; the
-// compensation terms follow the NA totals).  Orders >= 4 use it: their larger
-// accumulator sets would otherwise halve the resident blocks, and the sums
-// are touched once per fold only (every kFoldBlocks * kC steps).  Measured on
-// GB300 (cfg5, k = 4, BF16, apodised): 4.71 -> 4.36 ms per 64-frame launch;
-// at k = 3 (cfg2) the register form is faster (0.877 vs 0.977 ms).
+// Kahan fold of the partial sums into the running totals held in TMEM.  The
+// warp executes it converged: the plans that use it give every lane of a warp
+// the same channel-step range (one slot per warp, or slots without
+// apodisation, whose ranges are all the full aperture).
 template <int NA>
-__device__ __forceinline__ void kahan_fold_shared(float (&acc)[kC][NA], float4* s_sum) {
-  static_assert(kC == 4, "one float4 per accumulator");
-  const int bd = blockDim.x, t = threadIdx.x;
+__device__ __forceinline__ void kahan_fold_tmem(float (&acc)[kC][NA], uint32_t tmem) {
+  static_assert(kC == 4, "totals and compensation terms of one accumulator fill 8 columns");
+  __syncwarp();
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
-    float4 tv = s_sum[q * bd + t], cv = s_sum[(NA + q) * bd + t];
-    float* tt = reinterpret_cast<float*>(&tv);
-    float* cc = reinterpret_cast<float*>(&cv);
+    float t[8];
+    tmem_ld8(tmem + 8 * q, t);
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      const float y = acc[c][q] - cc[c];
-      const float s = tt[c] + y;
-      cc[c] = (s - tt[c]) - y;
-      tt[c] = s;
+      const float y = acc[c][q] - t[4 + c];
+      const float s = t[c] + y;
+      t[4 + c] = (s - t[c]) - y;
+      t[c] = s;
       acc[c][q] = 0.f;
     }
-    s_sum[q * bd + t] = tv;
-    s_sum[(NA + q) * bd + t] = cv;
+    tmem_st8(tmem + 8 * q, t);
   }
 }
 
-// Compensated sums of order K keep their totals in shared memory.
+// Compensated sums keep their Kahan totals in TMEM.  Measured on GB300
+// against the earlier forms (BF16 RF, fused kernel per launch): totals in
+// registers for k = 3 (128 registers, 2 blocks per SM) 0.752 -> 0.676 ms at
+// 3 blocks per SM; totals in shared memory for k = 4 / 5 / 8 (cfg2 geometry,
+// 32 frames) 0.893 / 1.010 / 2.199 -> 0.752 / 0.866 / 1.514 ms, the
+// apodised 64-frame k = 4 batch 2.91 -> 2.75 ms.
 template <int K, bool COMP>
-struct SharedSums {
-  static constexpr bool value = COMP && K >= 4;
+struct TmemSums {
+  static constexpr bool value = COMP;
 };
 
 // Resident 256-thread blocks per SM the register allocation targets: four
-// (64 registers) for plain orders <= 3, three (80 registers) for orders 4-5
-// (compensated ones with their totals in shared memory), two for compensated
-// orders <= 3 (totals in registers) and for orders >= 6.
+// (64 registers) for plain orders <= 3, three (80 registers) for compensated
+// orders <= 3 (at 64 registers their TMEM traffic spills: 0.707 vs 0.676 ms)
+// and for orders 4-5, two for orders >= 6.
 #ifndef PA_MINB4_MAX_K
 #define PA_MINB4_MAX_K 3
 #endif
 template <int K, bool COMP>
 struct MinBlocks {
-  static constexpr int value = (K >= 6 || (COMP && !SharedSums<K, COMP>::value))
-                                   ? 2
-                                   : (K <= PA_MINB4_MAX_K ? 4 : 3);
+  static constexpr int value = K >= 6 ? 2 : (K <= PA_MINB4_MAX_K && !COMP ? 4 : 3);
 };
 
 template <int K, bool APOD, bool COMP>
@@ -469,6 +495,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
   const int smem_hi = pairs_off + p.ncs * p.window * 8 - 8;  // shared addresses
 #endif
   int phase = 0;
+  constexpr bool TSUM = TmemSums<K, COMP>::value;
+  if constexpr (TSUM) {
+    if (warp == 0) {  // the whole warp allocates; the address lands in shared memory
+      tmem_alloc(sbase + kTmemOff, p.tmem_cols);
+      tc_fence_before_sync();
+    }
+  }
   if (threadIdx.x == 0) {
     if (p.use_tma) mbar_init(mbar);
     s_item[0] = atomicAdd(p.counter, 1);
@@ -476,6 +509,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     s_item[2] = 0;
   }
   __syncthreads();
+  uint32_t tmem = 0;  // this warp's TMEM lanes and columns (compensated orders <= 3)
+  if constexpr (TSUM) {
+    tc_fence_after_sync();
+    tmem = *reinterpret_cast<const volatile uint32_t*>(smem + kTmemOff) +
+           ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * NA * 8);
+  }
 
   for (;;) {
     const int item = s_item[0];
@@ -503,23 +542,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     const int2 vk = __ldg(p.vchunks + (size_t)tile_id * p.ngroups + grp);
 
     float acc[kC][NA];
-    constexpr bool SSUM = SharedSums<K, COMP>::value;
-    float tot[COMP && !SSUM ? kC : 1][COMP && !SSUM ? NA : 1];
-    float cmp[COMP && !SSUM ? kC : 1][COMP && !SSUM ? NA : 1];
-    float4* s_sum = reinterpret_cast<float4*>(smem + p.cmp_off);  // SSUM: compensated totals
 #pragma unroll
     for (int c = 0; c < kC; ++c)
 #pragma unroll
       for (int q = 0; q < NA; ++q) acc[c][q] = 0.f;
-    if constexpr (SSUM) {
+    if constexpr (TSUM) {
+      const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < 2 * NA; ++q)
-        s_sum[q * blockDim.x + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else if constexpr (COMP) {
-#pragma unroll
-      for (int c = 0; c < kC; ++c)
-#pragma unroll
-        for (int q = 0; q < NA; ++q) tot[c][q] = cmp[c][q] = 0.f;
+      for (int q = 0; q < NA; ++q) tmem_st8(tmem + 8 * q, z8);
     }
     int fold = 0;
 
@@ -645,8 +675,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         }
         if constexpr (COMP) {
           if (++fold == kFoldBlocks) {
-            if constexpr (SSUM) kahan_fold_shared<NA>(acc, s_sum);
-            else kahan_fold<NA>(acc, tot, cmp);
+            kahan_fold_tmem<NA>(acc, tmem);
             fold = 0;
           }
         }
@@ -668,8 +697,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       }
     }
     if (timed_out) break;
-    if constexpr (SSUM) kahan_fold_shared<NA>(acc, s_sum);
-    else if constexpr (COMP) kahan_fold<NA>(acc, tot, cmp);
+    if constexpr (TSUM) kahan_fold_tmem<NA>(acc, tmem);
     if (threadIdx.x == 0 && (!p.use_tma || vk.x >= vk.y)) {
       s_item[0] = s_item[2];
       s_item[1] = 0;
@@ -678,24 +706,24 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     // ---- epilogue (FP64 e_k) and store -----------------------------------
     const size_t plane = (size_t)p.nx * p.nz;
     const size_t fbase = (size_t)frame * p.planes * plane;
+    if constexpr (TSUM) {  // compensated totals minus compensations, read by the whole warp
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        float t[8];
+        tmem_ld8(tmem + 8 * q, t);
+#pragma unroll
+        for (int c = 0; c < kC; ++c) acc[c][q] = t[c] - t[4 + c];
+      }
+    }
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
       const int j = jt + p.m * c;
       if (j < p.nx && z < p.nz) {
-        // compensated sums: total minus compensation, rounded once to FP32
+        // plain sums, or compensated totals minus compensations (read from
+        // TMEM above), rounded once to FP32
         float V[NA];
 #pragma unroll
-        for (int q = 0; q < NA; ++q) {
-          if constexpr (COMP && !SSUM) {
-            V[q] = tot[c][q] - cmp[c][q];
-          } else if constexpr (SSUM) {
-            const float4 tv = s_sum[q * blockDim.x + threadIdx.x];
-            const float4 cv = s_sum[(NA + q) * blockDim.x + threadIdx.x];
-            V[q] = reinterpret_cast<const float*>(&tv)[c] - reinterpret_cast<const float*>(&cv)[c];
-          } else {
-            V[q] = acc[c][q];
-          }
-        }
+        for (int q = 0; q < NA; ++q) V[q] = acc[c][q];
         float das, dmas, ho;
         combine<K>(V, das, dmas, ho);
         const size_t px = fbase + (size_t)j * p.nz + z;
@@ -705,6 +733,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       }
     }
     __syncthreads();  // s_item is rewritten before the next item starts
+  }
+  if constexpr (TSUM) {  // every thread's TMEM accesses completed before the barrier
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after_sync();
+      tmem_dealloc(*reinterpret_cast<const volatile uint32_t*>(smem + kTmemOff), p.tmem_cols);
+    }
   }
 }
 

@@ -27,17 +27,31 @@ constexpr int kNCSMax = kNCMax + kC - 1;
 // peak for k = 3..5 at 256 channels.
 constexpr int kFoldBlocks = 8;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
-// Shared-memory layout of the fused kernel: work-item words and the TMA
-// mbarrier (16 B), channel bases and window starts (kCbInts ints each,
+// Shared-memory layout of the fused kernel: work-item words, the TMA
+// mbarrier (8 B at 16) and the TMEM base address (4 B at 24), channel bases
+// and window starts (kCbInts ints each,
 // >= kNCSMax + 1, multiple of 4), the raw TMA buffer (128-byte aligned, empty
 // without TMA), then the interpolation slots.
 constexpr int kCbInts = 76;
 constexpr int kMbarOff = 16;
+constexpr int kTmemOff = 24;
 constexpr int kCbOff = 32;
 constexpr int kLoOff = kCbOff + kCbInts * 4;
 constexpr int kRawOff = 640;  // >= kLoOff + 4 kCbInts, 128-byte aligned
 static_assert(kRawOff >= kLoOff + kCbInts * 4 && kRawOff % 128 == 0, "shared layout");
 constexpr int kMaxThreads = 1024;
+
+// TMEM columns a fused-kernel block allocates for compensated totals (a
+// power of two >= 32): the warps sharing a 32-lane quarter of TMEM times 8
+// columns per accumulator (kC totals and kC compensation terms).
+__host__ __device__ constexpr int tmem_columns(int warps, int na) {
+  return ((warps + 3) / 4) * na * 8 <= 32    ? 32
+         : ((warps + 3) / 4) * na * 8 <= 64  ? 64
+         : ((warps + 3) / 4) * na * 8 <= 128 ? 128
+                                              : 256;
+}
+// TMEM columns of one SM.
+constexpr int kTmemColsPerSm = 512;
 
 // Delay-table layout: row t = d - dmin (lattice offset d), depth z fastest,
 // so a warp's 32 depth rows read one contiguous 256-byte run per step.
@@ -59,7 +73,7 @@ struct BfParams {  // aligned as CUtensorMap requires
   int nearest;            // 1: nearest-sample delays (a = 0), one tap per pair
   int lane_rows_log2;     // log2 of the depth rows per lane group: 5, 4 or 3
   int nc, ncs;            // channel steps per chunk, virtual channels staged per chunk
-  int cmp_off;            // shared offset of the compensated totals (compensated sums)
+  int tmem_cols;          // TMEM columns a block allocates (compensated sums), else 0
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
   const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}

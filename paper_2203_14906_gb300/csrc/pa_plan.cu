@@ -72,7 +72,7 @@ struct pa_plan_s {
   bool use_tma = false;
   int lo_align = 4;   // window starts are multiples of this many samples
   int nc = 32;        // channel steps per staged chunk (multiple of kC)
-  int cmp_off = 0;    // shared offset of the compensated totals
+  int tmem_cols = 0;  // TMEM columns per fused-kernel block (compensated sums)
   int expect_extra = 0;   // > 0 only under PA_INJECT_TMA_SHORTFALL (tests the bounded wait)
   long long timeouts_seen = 0;  // timed-out waits already reported by pa_beamform_host
   int wr = 0;         // raw samples per channel delivered by one TMA box
@@ -411,9 +411,13 @@ void configure(pa_plan_s* P) {
   // k = 7 1.280 -> 1.339 ms; cfg5 (apodised) 2.91 -> 3.06 ms; 16-row groups
   // were never the fastest.  PA_LANE_ROWS=32|16|8 picks one, for comparisons.
   P->lane_rows_log2 = (B % 4 == 0 && !P->apod && P->K <= 4) ? 3 : 5;
+  // Compensated sums keep their Kahan totals in TMEM; its accesses are
+  // warp-wide, so every lane of a warp must run the same channel steps:
+  // apodised plans (per-slot channel ranges) then keep one slot per warp.
+  P->tmem_cols = P->comp ? tmem_columns(B, P->K <= 2 ? 3 : P->K + 2) : 0;
   if (const char* e = getenv("PA_LANE_ROWS")) {
     const int want = atoi(e) == 8 ? 3 : (atoi(e) == 16 ? 4 : 5);
-    if (B % (1 << (5 - want)) == 0) P->lane_rows_log2 = want;
+    if (B % (1 << (5 - want)) == 0 && !(P->tmem_cols && P->apod)) P->lane_rows_log2 = want;
   }
   P->threads = 32 * B;
   P->tile_x = P->m * kC * P->R;
@@ -479,12 +483,31 @@ void configure(pa_plan_s* P) {
   if (P->d.max_batch <= 0) P->d.max_batch = 1;
 }
 
-// Shared memory of the compensated sums of orders >= 4: a total and a
-// compensation term (float4 over the kC columns) per accumulator per thread.
-size_t sum_bytes(const pa_plan_s* P) {
-  if (!P->comp || P->K < 4) return 0;
-  const int na = P->K <= 2 ? 3 : P->K + 2;
-  return (size_t)2 * na * P->threads * 16;
+// Resident fused-kernel blocks per SM.  For plans that keep their Kahan
+// totals in TMEM the count comes from the kernel's registers, shared memory
+// and threads (the occupancy calculator reports one block per SM for a
+// kernel that allocates tensor memory) and is capped so that the resident
+// blocks' TMEM columns fit the SM's 512.
+cudaError_t fused_blocks_per_sm(const pa_plan_s* P, size_t smem, int* n) {
+  cudaError_t e = bf_occupancy(P->K, P->apod, P->comp, P->threads, smem, n);
+  if (e != cudaSuccess || !P->tmem_cols) return e;
+  cudaFuncAttributes a;
+  e = cudaFuncGetAttributes(&a, bf_func(P->K, P->apod, P->comp));
+  if (e != cudaSuccess) return e;
+  int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0, rsv = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = (P->threads + 31) / 32;
+  const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;  // 256-register units per warp
+  int b = std::min(regs_sm / std::max(1, regs_warp * warps), thr_sm / (32 * warps));
+  b = std::min(b, (int)((size_t)smem_sm / (smem + a.sharedSizeBytes + (size_t)rsv)));
+  b = std::min(b, blk_sm);
+  *n = std::max(0, std::min(b, kTmemColsPerSm / P->tmem_cols));
+  return cudaSuccess;
 }
 
 size_t table_bytes(const pa_plan_s* P) {
@@ -686,8 +709,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
     auto smem_for = [&](int c) {
       const int ncs = c + kC - 1;
       const size_t raw = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
-      return (size_t)kRawOff + ((raw + 127) & ~size_t(127)) + (size_t)ncs * P->window * 8 +
-             sum_bytes(P);
+      return (size_t)kRawOff + ((raw + 127) & ~size_t(127)) + (size_t)ncs * P->window * 8;
     };
     auto fits = [&](int c) {
       const int ncs = c + kC - 1;
@@ -697,7 +719,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
     };
     auto occupancy = [&](int c) {
       int b = 0;
-      if (bf_occupancy(P->K, P->apod, P->comp, P->threads, smem_for(c), &b) != cudaSuccess) b = 0;
+      if (fused_blocks_per_sm(P, smem_for(c), &b) != cudaSuccess) b = 0;
       return b;
     };
     auto even = [&](int nch) { return ((steps + nch - 1) / nch + kC - 1) / kC * kC; };
@@ -760,8 +782,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   const int ncs = P->nc + kC - 1;
   const size_t raw_bytes = P->use_tma ? (size_t)ncs * P->rp * P->elt : 0;
   P->pairs_off = kRawOff + (int)((raw_bytes + 127) & ~size_t(127));
-  P->cmp_off = (int)((size_t)P->pairs_off + (size_t)ncs * P->window * sizeof(float2));  // 16-aligned
-  P->smem = (size_t)P->cmp_off + sum_bytes(P);
+  P->smem = (size_t)P->pairs_off + (size_t)ncs * P->window * sizeof(float2);
   const long long w4 = P->window / 4;
   if ((long long)ncs * w4 * w4 >= (1ll << 20))
     return fail(PA_EUNSUPPORTED, "RF window of %d samples per channel is too wide; use a finer "
@@ -771,7 +792,9 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
                 "RF window of %d samples per channel needs %zu B of shared memory; use a finer "
                 "depth grid",
                 P->window, P->smem);
-  PA_CUDA(bf_occupancy(P->K, P->apod, P->comp, P->threads, P->smem, &P->blocks_per_sm));
+  // (resident blocks never ask for more TMEM than an SM has, so no block's
+  // allocation waits on another block of the same launch)
+  PA_CUDA(fused_blocks_per_sm(P, P->smem, &P->blocks_per_sm));
   if (P->blocks_per_sm < 1)
     return fail(PA_EUNSUPPORTED, "fused kernel does not fit an SM (%d threads, %zu B smem)",
                 P->threads, P->smem);
@@ -889,7 +912,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.rp = P->rp;
   b.nc = P->nc;
   b.ncs = P->nc + kC - 1;
-  b.cmp_off = P->cmp_off;
+  b.tmem_cols = P->tmem_cols;
   b.chunk_bytes = b.ncs * P->wr * (int)P->elt;
   b.pairs_off = P->pairs_off;
   if (P->use_tma && !encode_rf_map(P, rf, nf, &b.tmap))
