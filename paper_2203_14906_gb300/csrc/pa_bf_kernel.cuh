@@ -16,7 +16,8 @@
 //            reproduces the rule "s = 0 when a tap leaves the record".
 // Per pair the arithmetic is FP32: interpolation, apodisation, one MUFU
 // lg2/ex2 (or rsqrt) pair for the roots, power sums; Kahan-compensated
-// sums are folded every kFoldBlocks*kC channels when requested.  Per pixel,
+// sums are folded every kFoldBlocks*kC channels when requested, into totals
+// held in tensor memory (TMEM).  Per pixel,
 // the power sums p_1..p_k are turned into e_k in FP64 (see combine).
 #pragma once
 
