@@ -126,6 +126,10 @@ typedef struct {
   int32_t lane_rows;          /* depth rows per lane group of the fused
                                  kernel (32, 16 or 8; a warp covers
                                  32 / lane_rows neighbouring slots)        */
+  int32_t tmem_columns;       /* tensor-memory columns each fused-kernel
+                                 block allocates for the Kahan totals of
+                                 compensated sums (0: plain sums); resident
+                                 blocks per SM x tmem_columns <= 512       */
 } pa_plan_info;
 
 /*

@@ -111,6 +111,7 @@ class PlanInfo(ctypes.Structure):
         ("device_error_flags", ctypes.c_uint32),
         ("chunk_steps", ctypes.c_int32),
         ("lane_rows", ctypes.c_int32),
+        ("tmem_columns", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -1448,6 +1448,7 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->tma_staging = P->use_tma ? 1 : 0;
   info->chunk_steps = P->nc;
   info->lane_rows = 1 << P->lane_rows_log2;
+  info->tmem_columns = P->tmem_cols;
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);

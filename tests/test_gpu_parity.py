@@ -350,6 +350,50 @@ def test_lane_groups_keep_bits(monkeypatch):
         assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+def test_lane_groups_with_tmem_sums(monkeypatch):
+    """Compensated sums keep their Kahan totals in tensor memory, read and
+    written warp-wide: without apodisation every lane grouping gives the same
+    bits; with apodisation the plan keeps one slot per warp whatever
+    PA_LANE_ROWS asks for, and the results match the oracle."""
+    wl = synth.workload("cfg1")
+    rf = _frames(wl, [4])
+    outs = []
+    for rows in ("32", "16", "8"):
+        monkeypatch.setenv("PA_LANE_ROWS", rows)
+        out, info, _ = run_gpu(wl, rf, 3, rf_dtype="bf16", compensated=1)
+        assert info["device_error_flags"] == 0 and info["lane_rows"] == int(rows)
+        outs.append(out)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    wl_a = synth.workload("cfg1", f_number=1.5)
+    rf_a = _frames(wl_a, [5])
+    monkeypatch.setenv("PA_LANE_ROWS", "8")
+    out, info, deq = run_gpu(wl_a, rf_a, 4, rf_dtype="bf16", compensated=1)
+    assert info["lane_rows"] == 32 and info["device_error_flags"] == 0
+    assert_parity(compare(out, oracle_frames(wl_a, deq, 4)), TOL32, what="apodised, TMEM sums")
+
+
+def test_tmem_residency_fits_the_sm():
+    """Resident blocks per SM times the TMEM columns each block allocates
+    stay within the SM's 512 columns (no block's allocation waits on another
+    block of the same launch), for compensated plans of every order and the
+    benchmark geometries; plain plans allocate none."""
+    import paper_2203_14906_gb300 as pa
+
+    for name, k in (("cfg1", 1), ("cfg1", 3), ("cfg2", 3), ("cfg2", 5), ("cfg2", 8), ("cfg3", 5),
+                    ("cfg5", 4)):
+        wl = synth.workload(name)
+        for comp in (0, 1):
+            with pa.Plan(pa.make_desc(wl, order_k=k, outputs=7, rf_dtype="bf16",
+                                      compensated=comp)) as plan:
+                info = plan.info()
+            if comp:
+                assert info["tmem_columns"] in (32, 64, 128, 256), (name, k)
+                assert info["blocks_per_sm"] * info["tmem_columns"] <= 512, (name, k, info)
+                assert info["blocks_per_sm"] >= 2 or k >= 6, (name, k, info)
+            else:
+                assert info["tmem_columns"] == 0
+
+
 def test_long_columns_and_odd_width():
     """nz > 1024 (2048-point envelope transforms, the out-of-place FFT path),
     an odd number of columns (the last column pair has one column) and a
