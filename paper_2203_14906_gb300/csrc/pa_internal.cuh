@@ -147,6 +147,10 @@ void post_spec(const PostParams& p, LaunchSpec* s);
 // it are radix 8, then one radix-4 or radix-2 pass for the remainder); the
 // host builds the per-pass twiddle tables in the same order.
 __host__ __device__ constexpr int post_first_radix(int m) { return m == 1024 ? 16 : 8; }
+// Post-kernel buffers keep one padding slot every 2^post_pad_shift(M)
+// complex elements (16 from 256 points on, else 8).
+__host__ __device__ constexpr int post_pad_shift(int m) { return m >= 256 ? 4 : 3; }
+__host__ __device__ constexpr int post_padded_len(int m) { return m + (m >> post_pad_shift(m)); }
 int post_buffers(int m);     // M-point complex buffers per team of the post kernel
 const void* post_inplace_func(int m);  // in-place kernel for M points, or nullptr
 int post_team_warps(int m);  // warps per team (column pair) of the post kernel

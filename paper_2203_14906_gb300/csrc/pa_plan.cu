@@ -446,7 +446,7 @@ void configure(pa_plan_s* P) {
   // post_team_warps warps, plus the twiddles and mask), in whole teams
   {
     const int tw_warps = post_team_warps(P->M);
-    const size_t per_team = (size_t)post_buffers(P->M) * (P->M + P->M / 8) * sizeof(float2);
+    const size_t per_team = (size_t)post_buffers(P->M) * post_padded_len(P->M) * sizeof(float2);
     const size_t tw = (size_t)P->M * (sizeof(float2) + sizeof(float));  // twiddles + mask
     const size_t sm_bytes = 227 * 1024;
     int best = tw_warps;
@@ -833,7 +833,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   PA_CUDA(cudaMemcpyAsync(P->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
   PA_CUDA(cudaMemcpyAsync(P->mask, mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice,
                           st));
-  // post kernel: (3 post_wpb (M + M/8) + M) * 8 bytes, at most 200 KiB
+  // post kernel: (3 post_wpb post_padded_len(M) + M) * 8 bytes, at most 200 KiB
   PA_CUDA(post_configure((size_t)200 * 1024));
   PA_CUDA(cudaStreamSynchronize(st));
   return PA_OK;

@@ -116,10 +116,17 @@ __device__ __forceinline__ void dft_any(float2 (&x)[R]) {
   else dft_regs<R>(x);
 }
 
-// Shared buffers hold element i at i + i/8: one padding slot every eight
-// elements keeps the strided stores of the first passes (stride R elements)
-// free of multi-way bank conflicts.
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+// Shared buffers hold element i at pidx(i, ps) = i + (i >> ps): one padding
+// slot every 2^ps elements (post_pad_shift).  From 256 points on, one slot
+// per 16: a half-warp's 64-bit access covers 16 elements (128 bytes), so the
+// contiguous accesses, the first passes' stores (stride 8 or 16) and the
+// strided passes are all free of bank conflicts (one slot per 8 left every
+// contiguous access 2-way conflicted; counted on the kernel's access pattern
+// per column pair: 768 -> 608 wavefronts at 512 points, 1920 -> 1024 at
+// 1024 points; measured 0.107 -> 0.097 ms and 1.07 -> 0.94 ms per launch).
+// Below 256 points one slot per 8 measured faster (more of their passes have
+// sub-transform lengths of 8).
+__device__ __forceinline__ int pidx(int i, int ps) { return i + (i >> ps); }
 
 // Twiddle tables are stored per pass in access order: the pass over
 // sub-transforms of length ns (> 1) with radix R owns ns (R - 1) entries,
@@ -135,23 +142,24 @@ __device__ __forceinline__ void twiddles(const float2* twp, int k, float2 (&w)[R
 // One Stockham pass of radix R over sub-transforms of length ns.
 template <int R>
 __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int m, int ns,
-                                              const float2* twp, int lane) {
+                                              const float2* twp, int lane, int ps) {
   const int groups = m / R;
-  // With groups a multiple of 8, pidx(j + r groups) = pidx(j) + r (groups +
-  // groups / 8); with ns = 1 or a multiple of 8 the same holds for the
-  // stores.  (Both hold for every pass once M >= 64.)
-  const bool strided = (groups & 7) == 0 && (ns == 1 || (ns & 7) == 0);
-  const int is = groups + (groups >> 3), os = ns + (ns >> 3);
+  // With groups a multiple of 2^ps, pidx(j + r groups) = pidx(j) + r (groups
+  // + groups / 2^ps); with ns = 1 or a multiple of 2^ps the same holds for
+  // the stores.  Other passes index every element.
+  const int pm = (1 << ps) - 1;
+  const bool strided = (groups & pm) == 0 && (ns == 1 || (ns & pm) == 0);
+  const int is = groups + (groups >> ps), os = ns + (ns >> ps);
   for (int j = lane; j < groups; j += 32) {
     const int k = j & (ns - 1);
     float2 x[R];
     if (strided) {
-      const float2* ip = in + pidx(j);
+      const float2* ip = in + pidx(j, ps);
 #pragma unroll
       for (int r = 0; r < R; ++r) x[r] = ip[r * is];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[r] = in[pidx(j + r * groups)];
+      for (int r = 0; r < R; ++r) x[r] = in[pidx(j + r * groups, ps)];
     }
     if (ns > 1) {
       float2 w[R];
@@ -162,19 +170,19 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
     dft_regs<R>(x);
     const int base = (j - k) * R + k;
     if (strided) {
-      float2* op = out + pidx(base);
+      float2* op = out + pidx(base, ps);
 #pragma unroll
       for (int r = 0; r < R; ++r) op[r * os] = x[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[pidx(base + r * ns)] = x[r];
+      for (int r = 0; r < R; ++r) out[pidx(base + r * ns, ps)] = x[r];
     }
   }
 }
 
 // Forward FFT of buf_a; returns the buffer (buf_a or buf_b) holding the result.
 __device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, const float2* tw,
-                               int lane) {
+                               int lane, int ps) {
   // tw: shared-memory copy of e^{-2 pi i k / m}, k < m
   float2* in = buf_a;
   float2* out = buf_b;
@@ -182,17 +190,17 @@ __device__ float2* fft_forward(float2* buf_a, float2* buf_b, int m, int log2m, c
   const float2* twp = tw;  // per-pass twiddle blocks, in pass order
   while (rem > 0) {
     if (rem >= 3) {
-      stockham_pass<8>(in, out, m, ns, twp, lane);
+      stockham_pass<8>(in, out, m, ns, twp, lane, ps);
       if (ns > 1) twp += ns * 7;
       ns *= 8;
       rem -= 3;
     } else if (rem == 2) {
-      stockham_pass<4>(in, out, m, ns, twp, lane);
+      stockham_pass<4>(in, out, m, ns, twp, lane, ps);
       if (ns > 1) twp += ns * 3;
       ns *= 4;
       rem -= 2;
     } else {
-      stockham_pass<2>(in, out, m, ns, twp, lane);
+      stockham_pass<2>(in, out, m, ns, twp, lane, ps);
       if (ns > 1) twp += ns;
       ns *= 2;
       rem -= 1;
@@ -230,21 +238,22 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
                                                       const Team& tm) {
   constexpr int TL = 32 * TW;
   constexpr int GPL = (32 * MPL / R) >= TL ? (32 * MPL / R) / TL : 1;  // groups per team lane
+  constexpr int PS = post_pad_shift(32 * MPL), PM = (1 << PS) - 1;
   const int groups = m / R;
-  const int is = groups + (groups >> 3), os = ns + (ns >> 3);
-  const bool strided = (groups & 7) == 0 && (ns == 1 || (ns & 7) == 0);
+  const int is = groups + (groups >> PS), os = ns + (ns >> PS);
+  const bool strided = (groups & PM) == 0 && (ns == 1 || (ns & PM) == 0);
   float2 x[GPL][R];
 #pragma unroll
   for (int t = 0; t < GPL; ++t) {
     const int j = tm.tl + TL * t;
     if (j < groups) {
       if (strided) {
-        const float2* ip = buf + pidx(j);
+        const float2* ip = buf + pidx(j, PS);
 #pragma unroll
         for (int r = 0; r < R; ++r) x[t][r] = ip[r * is];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[t][r] = buf[pidx(j + r * groups)];
+        for (int r = 0; r < R; ++r) x[t][r] = buf[pidx(j + r * groups, PS)];
       }
     }
   }
@@ -263,12 +272,12 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
       dft_regs<R>(x[t]);
       const int base = (j - k) * R + k;
       if (strided) {
-        float2* op = buf + pidx(base);
+        float2* op = buf + pidx(base, PS);
 #pragma unroll
         for (int r = 0; r < R; ++r) op[r * os] = x[t][r];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pidx(base + r * ns)] = x[t][r];
+        for (int r = 0; r < R; ++r) buf[pidx(base + r * ns, PS)] = x[t][r];
       }
     }
   }
@@ -308,6 +317,7 @@ template <int MPL, int TW>
 __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* ca, const float* cb,
                                                         int nz, bool two, const Team& tm) {
   using S = PostShape<MPL, TW>;
+  constexpr int PS = post_pad_shift(S::M);
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
     const int j = tm.tl + S::TL * t;
@@ -321,10 +331,11 @@ __device__ __forceinline__ void first_pass_from_columns(float2* A, const float* 
       x[r] = make_float2(in ? ca[n] : 0.f, (in && two) ? cb[n] : 0.f);
     }
     dft_any<R>(x);
-    // outputs R j + r: pidx(R j + r) = pidx(R j) + r + r / 8 (R j is a multiple of 8)
-    float2* op = A + pidx(R * j);
+    // outputs R j + r: pidx(R j + r) = pidx(R j) + r (R j is a multiple of
+    // 2^PS, or of 8 with r < 8)
+    float2* op = A + pidx(R * j, PS);
 #pragma unroll
-    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = x[r];
+    for (int r = 0; r < R; ++r) op[r] = x[r];
   }
   team_sync<TW>(tm);
 }
@@ -338,7 +349,7 @@ template <int MPL, int TW>
 __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const float* mk,
                                                  const Team& tm) {
   using S = PostShape<MPL, TW>;
-  constexpr int M = S::M, R = S::R1;
+  constexpr int M = S::M, R = S::R1, PS = post_pad_shift(M);
   float2 xa[S::GPL][R];
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
@@ -348,15 +359,15 @@ __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const flo
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = j + r * S::G1;
-      const float2 zn = A[pidx(n)], zm = A[pidx((M - n) & (M - 1))];
+      const float2 zn = A[pidx(n, PS)], zm = A[pidx((M - n) & (M - 1), PS)];
       const float h = 0.5f * mk[n];
       xa[t][r] = make_float2(h * (zn.x + zm.x), -h * (zn.y - zm.y));
       xb[r] = make_float2(h * (zn.y + zm.y), h * (zn.x - zm.x));
     }
     dft_any<R>(xb);
-    float2* op = B + pidx(R * j);
+    float2* op = B + pidx(R * j, PS);
 #pragma unroll
-    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = xb[r];
+    for (int r = 0; r < R; ++r) op[r] = xb[r];
   }
   team_sync<TW>(tm);
 #pragma unroll
@@ -364,9 +375,9 @@ __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const flo
     const int j = tm.tl + S::TL * t;
     if (j >= S::G1) break;
     dft_any<R>(xa[t]);
-    float2* op = A + pidx(R * j);
+    float2* op = A + pidx(R * j, PS);
 #pragma unroll
-    for (int r = 0; r < R; ++r) op[r + (r >> 3)] = xa[t][r];
+    for (int r = 0; r < R; ++r) op[r] = xa[t][r];
   }
   team_sync<TW>(tm);
 }
@@ -378,15 +389,22 @@ template <int R, int MPL, int TW>
 __device__ __forceinline__ void last_pass_to_column(const float2* buf, const float2* twp, float* col,
                                                     int nz, float inv_m, float& mx, const Team& tm) {
   constexpr int M = 32 * MPL, ns = M / R, groups = M / R, TL = 32 * TW;
-  constexpr int is = groups + (groups >> 3);
+  constexpr int PS = post_pad_shift(M);
+  constexpr bool strided = (groups & ((1 << PS) - 1)) == 0;
+  constexpr int is = groups + (groups >> PS);
 #pragma unroll
   for (int t = 0; t < (groups + TL - 1) / TL; ++t) {
     const int j = tm.tl + TL * t;
     if (j >= groups) break;
     float2 x[R];
-    const float2* ip = buf + pidx(j);
+    if constexpr (strided) {
+      const float2* ip = buf + pidx(j, PS);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = ip[r * is];
+      for (int r = 0; r < R; ++r) x[r] = ip[r * is];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = buf[pidx(j + r * groups, PS)];
+    }
     float2 w[R];
     twiddles<R>(twp, j, w);
 #pragma unroll
@@ -437,7 +455,7 @@ __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   extern __shared__ __align__(16) float2 sbuf[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int M = 32 * MPL;
-  constexpr int MP = M + (M >> 3);
+  constexpr int MP = post_padded_len(M);
   float2* tw = sbuf;  // p.n_tw per-pass twiddles, then the mask, then buffers
   float* mk = reinterpret_cast<float*>(sbuf + p.n_tw);
   for (int k = threadIdx.x; k < p.n_tw; k += blockDim.x) tw[k] = __ldg(p.tw + k);
@@ -476,7 +494,8 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
   extern __shared__ __align__(16) float2 sbuf[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = p.m;
-  const int MP = M + (M >> 3);  // padded buffer length
+  const int ps = post_pad_shift(M);
+  const int MP = post_padded_len(M);  // padded buffer length
   float2* tw = sbuf;  // p.n_tw per-pass twiddles, then the buffers
   for (int k = threadIdx.x; k < p.n_tw; k += blockDim.x) tw[k] = __ldg(p.tw + k);
   __syncthreads();
@@ -501,21 +520,21 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
         a = *reinterpret_cast<const float4*>(src + n);
         if (two) b = *reinterpret_cast<const float4*>(src + p.nz + n);
       }
-      b0[pidx(n)] = make_float2(a.x, b.x);
-      b0[pidx(n + 1)] = make_float2(a.y, b.y);
-      b0[pidx(n + 2)] = make_float2(a.z, b.z);
-      b0[pidx(n + 3)] = make_float2(a.w, b.w);
+      b0[pidx(n, ps)] = make_float2(a.x, b.x);
+      b0[pidx(n + 1, ps)] = make_float2(a.y, b.y);
+      b0[pidx(n + 2, ps)] = make_float2(a.z, b.z);
+      b0[pidx(n + 3, ps)] = make_float2(a.w, b.w);
     }
   } else {
     for (int n = lane; n < M; n += 32) {
       const bool in_col = n < p.nz;
       const float a = in_col ? src[n] : 0.f;
       const float b = (in_col && two) ? src[p.nz + n] : 0.f;
-      b0[pidx(n)] = make_float2(a, b);
+      b0[pidx(n, ps)] = make_float2(a, b);
     }
   }
   __syncwarp();
-  float2* Z = fft_forward(b0, b1, M, p.log2m, tw, lane);
+  float2* Z = fft_forward(b0, b1, M, p.log2m, tw, lane, ps);
   float2* F = (Z == b0) ? b1 : b0;  // free buffer
 
   // Split the packed spectrum and apply the mask.  Bins k and M-k are handled
@@ -525,20 +544,20 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
   const int half = M >> 1;
   for (int k = lane; k <= half; k += 32) {
     const int km = (M - k) & (M - 1);
-    const float2 z = Z[pidx(k)], zc = Z[pidx(km)];
+    const float2 z = Z[pidx(k, ps)], zc = Z[pidx(km, ps)];
     const float hk = 0.5f * __ldg(mk + k);
     // A[k] = (z + conj zc) / 2,  B[k] = (z - conj zc) / (2i)
-    b2[pidx(k)] = make_float2(hk * (z.x + zc.x), -hk * (z.y - zc.y));
-    Z[pidx(k)] = make_float2(hk * (z.y + zc.y), hk * (z.x - zc.x));
+    b2[pidx(k, ps)] = make_float2(hk * (z.x + zc.x), -hk * (z.y - zc.y));
+    Z[pidx(k, ps)] = make_float2(hk * (z.y + zc.y), hk * (z.x - zc.x));
     if (km != k) {
       const float hm = 0.5f * __ldg(mk + km);  // zero for km > M/2
-      b2[pidx(km)] = make_float2(hm * (zc.x + z.x), -hm * (zc.y - z.y));
-      Z[pidx(km)] = make_float2(hm * (zc.y + z.y), hm * (zc.x - z.x));
+      b2[pidx(km, ps)] = make_float2(hm * (zc.x + z.x), -hm * (zc.y - z.y));
+      Z[pidx(km, ps)] = make_float2(hm * (zc.y + z.y), hm * (zc.x - z.x));
     }
   }
   __syncwarp();
   const float inv_m = 1.0f / (float)M;
-  const float2* Ya = fft_forward(b2, F, M, p.log2m, tw, lane);
+  const float2* Ya = fft_forward(b2, F, M, p.log2m, tw, lane, ps);
   float mx = 0.f;
   auto emit = [&](const float2* Y, float* col) {
     if (vec) {
@@ -546,7 +565,7 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
         float e[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const float2 y = Y[pidx(n + t)];
+          const float2 y = Y[pidx(n + t, ps)];
           e[t] = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
           mx = fmaxf(mx, e[t]);
         }
@@ -554,7 +573,7 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
       }
     } else {
       for (int n = lane; n < p.nz; n += 32) {
-        const float2 y = Y[pidx(n)];
+        const float2 y = Y[pidx(n, ps)];
         const float env = sqrtf(y.x * y.x + y.y * y.y) * inv_m;
         col[n] = env;
         mx = fmaxf(mx, env);
@@ -567,7 +586,7 @@ __global__ void __launch_bounds__(256) k_post(const PostParams p) {
     // Ya lives in b2 or F; the FFT of the B half ping-pongs between Z and the
     // buffer Ya does not use.
     float2* G = (Ya == b2) ? F : b2;
-    emit(fft_forward(Z, G, M, p.log2m, tw, lane), dst + p.nz);
+    emit(fft_forward(Z, G, M, p.log2m, tw, lane, ps), dst + p.nz);
   }
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
@@ -632,7 +651,7 @@ int post_team_warps(int m) {
 }
 
 void post_spec(const PostParams& p, LaunchSpec* ls) {
-  const size_t mp = (size_t)p.m + (p.m >> 3);
+  const size_t mp = (size_t)post_padded_len(p.m);
   const void* f = post_inplace_func(p.m);
   ls->func = f ? f : reinterpret_cast<const void*>(k_post);
   // in place: two buffers per team of post_team_warps warps; fallback: three
