@@ -381,7 +381,7 @@ __device__ __forceinline__ ItemInfo decode_item(const BfParams& p, int item) {
   return it;
 }
 
-// ---- Tensor memory (TMEM) for the compensated totals of orders <= 3 -------
+// ---- Tensor memory (TMEM) for the Kahan totals of compensated sums -------
 // The kernel does no matrix work, so the SM's 256 KB of tensor memory is
 // free to hold the Kahan totals and compensation terms.  Warp w reaches TMEM
 // lanes 32 (w % 4) .. 32 (w % 4) + 31 (lane = its own lane); warps w and
