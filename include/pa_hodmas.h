@@ -91,7 +91,8 @@ typedef struct {
                             otherwise the order-dependent default band      */
   double band_hi_hz;     /* < 0: band-pass off (analytic mask only)         */
   double dyn_range_db;   /* log-compression range; <= 0 means 60 dB        */
-  int32_t compensated;   /* 1: Kahan-compensated FP32 power sums            */
+  int32_t compensated;   /* 1: Kahan-compensated FP32 power sums (totals
+                            and compensation terms kept in tensor memory) */
   pa_interp interp;      /* sampling of the delayed signal                  */
 } pa_plan_desc;
 
