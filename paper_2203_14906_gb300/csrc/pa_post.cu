@@ -608,10 +608,16 @@ __global__ void __launch_bounds__(256) k_log(const LogParams p) {
     const long long n4 = p.plane_elems >> 2;
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
-    for (long long q = t0; q < n4; q += stride) {
+    // two loads in flight per thread before either result is stored
+    for (long long q = t0; q < n4; q += 2 * stride) {
+      const long long q1 = q + stride;
       const float4 e = s4[q];
+      const float4 e1 = q1 < n4 ? s4[q1] : e;
       d4[q] = make_float4(log_db(e.x, mx, inv, dr), log_db(e.y, mx, inv, dr),
                           log_db(e.z, mx, inv, dr), log_db(e.w, mx, inv, dr));
+      if (q1 < n4)
+        d4[q1] = make_float4(log_db(e1.x, mx, inv, dr), log_db(e1.y, mx, inv, dr),
+                             log_db(e1.z, mx, inv, dr), log_db(e1.w, mx, inv, dr));
     }
   } else {
     for (long long q = t0; q < p.plane_elems; q += stride) dst[q] = log_db(src[q], mx, inv, dr);
