@@ -13,6 +13,13 @@ in HBM, L2 flushed by a 256 MiB write between steps, outside the events).
 log images out, copies inside the timed region).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+
+``--case WORKLOAD`` (for profiling one configuration under ncu, or with
+CUDA-event timing alone) runs that workload's launch sequence ``--launches``
+times after ``--warmup`` launches on seeded random RF of its shape (the
+arithmetic does not depend on the values), each launch after a 256 MiB L2
+flush, and prints its kernel times, e.g. ``python bench.py --case cfg5
+--frames 4``.
 """
 
 from __future__ import annotations
@@ -43,8 +50,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--frames", type=int, default=32)
-    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--frames", type=int, default=None,
+                    help="frames per step (default 32; with --case, the workload's)")
+    ap.add_argument("--order", type=int, default=None,
+                    help="order k (default 3; with --case, the workload's)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip precision form and cpu baseline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -53,7 +62,20 @@ def parse():
     ap.add_argument("--form", default="fp32", choices=["fp32", "precision"],
                     help="arithmetic form of the headline leg: FP32 RF and plain sums, or BF16 "
                          "RF with Kahan-compensated sums")
-    return ap.parse_args()
+    ap.add_argument("--case", default=None, choices=["cfg1", "cfg2", "cfg3", "cfg5"],
+                    help="profile one workload's launch sequence instead of the benchmark")
+    ap.add_argument("--rf", default=None, choices=["f32", "bf16", "f16"],
+                    help="--case: RF storage type (default: the workload's)")
+    ap.add_argument("--compensated", type=int, default=None, choices=[0, 1],
+                    help="--case: Kahan-compensated sums (default: the workload's)")
+    ap.add_argument("--nx", type=int, default=None, help="--case: lateral pixels")
+    ap.add_argument("--nz", type=int, default=None, help="--case: depth pixels")
+    ap.add_argument("--launches", type=int, default=3, help="--case: timed launches")
+    args = ap.parse_args()
+    if args.case is None:
+        args.frames = 32 if args.frames is None else args.frames
+        args.order = 3 if args.order is None else args.order
+    return args
 
 
 def form_dtype(args):
@@ -438,7 +460,7 @@ def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
 
 def metrics_rois(wl):
     """Ten target discs (r = 0.5 mm) in five depth pairs, the layout of the
-    paper's point-target phantom (Section 4), each with a 1-2 mm annulus as
+    paper's simulated phantom (Section 3), each with a 1-2 mm annulus as
     background."""
     w = wl["x1_m"] - wl["x0_m"]
     h = wl["z1_m"] - wl["z0_m"]
@@ -759,8 +781,58 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """One workload's launch sequence, timed per kernel (see the module
+    docstring); no oracle, no extras."""
+    import torch
+
+    import synth
+    import paper_2203_14906_gb300 as pa
+
+    over = {kk: v for kk, v in (("nx", args.nx), ("nz", args.nz)) if v is not None}
+    wl = synth.workload(args.case, **over)
+    F = args.frames or int(wl.get("n_frames", 1))
+    k = args.order or int(wl.get("order_k", 3))
+    rf_dtype = args.rf or wl.get("rf_dtype", "f32")
+    comp = args.compensated if args.compensated is not None else int(wl.get("compensated", 0))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    x = torch.randn(F, wl["n_elem"], wl["n_samples"], device=dev, generator=g)
+    rf = x.to({"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[rf_dtype])
+    desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype=rf_dtype, max_batch=F, compensated=comp)
+    with pa.Plan(desc, stream=stream) as plan, torch.cuda.stream(stream):
+        out = torch.empty(plan.out_shape(F, pa.PA_STAGE_LOG), dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            flush.zero_()
+            pa.beamform(plan, rf, pa.PA_STAGE_LOG, out=out, stream=stream)
+        stream.synchronize()
+        plan.profile_read()
+        plan.profile(True)
+        for _ in range(args.launches):
+            flush.zero_()
+            pa.beamform(plan, rf, pa.PA_STAGE_LOG, out=out, stream=stream)
+        stream.synchronize()
+        prof = plan.profile_read()
+        plan.profile(False)
+        info = plan.info()
+    print(json.dumps({
+        "case": args.case, "grid": [wl["nx"], wl["nz"]], "frames": F, "order_k": k,
+        "rf": rf_dtype, "compensated": comp,
+        "kernels_ms_per_launch": {kk: v[0] / max(v[1], 1) for kk, v in prof.items()},
+        "plan": {f: info[f] for f in LAUNCH_FIELDS + ("lattice_m", "tmem_columns")},
+        "nominal_pairs": info["nominal_pairs"] * F, "active_pairs": info["active_pairs"] * F,
+        "device_error_flags": info["device_error_flags"],
+    }), flush=True)
+    return 0 if info["device_error_flags"] == 0 else 1
+
+
 def main():
     args = parse()
+    if args.case is not None:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

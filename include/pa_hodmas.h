@@ -149,9 +149,13 @@ typedef struct {
  * on the first three): PA_STAGING=tma|loads picks the RF staging path (TMA
  * boxes need Ns to be a multiple of the window alignment), PA_CHUNK_STEPS=n
  * caps the channel steps per staged chunk, PA_LANE_ROWS=32|16|8 sets the
- * depth rows per lane group of the fused kernel, PA_INJECT_TMA_SHORTFALL makes
+ * depth rows per lane group of the fused kernel.  In the checked build only
+ * (device bounds checks, PA_CHECK_BOUNDS), PA_INJECT_TMA_SHORTFALL makes
  * every TMA chunk expect 16 bytes more than it receives, so each block's
- * bounded wait runs out (failure-detection tests).
+ * bounded wait runs out (failure-detection tests); the release build ignores
+ * it.  After a PA_ETIMEOUT that was not injected (a copy that never
+ * arrived), copies may still be in flight into the stopped blocks' shared
+ * memory: destroy the plan and treat the CUDA context as suspect.
  */
 pa_status pa_plan(const pa_plan_desc* desc, void* cuda_stream, pa_plan_t* out);
 
@@ -361,7 +365,7 @@ pa_status pa_server_get_stats(pa_server_t srv, pa_server_stats* stats);
 pa_status pa_server_destroy(pa_server_t srv);
 
 /* ------------------------------------------------------------------------
- * Image-quality metrics of Section 4 on images already in device memory:
+ * Image-quality metrics of Section 3 on images already in device memory:
  * SNR (Eq. 10), CR (Eq. 11), gCNR (Eq. 12) and the lateral FWHM of a
  * target's main lobe.  Meant for envelope images (the ENV stage, linear
  * amplitude), which is what the paper's PA signal amplitudes are.
@@ -453,11 +457,15 @@ pa_status pa_destroy(pa_plan_t plan);
  *             count as 0), device memory, caller-owned, read only.
  *   log_dev   [n_images][image_elems] FP32 output, caller-owned; may equal
  *             env_dev (in place).
+ *   dyn_range_db  clipping range in dB; not positive (or NaN) means 60 dB,
+ *             as in pa_plan_desc.
  * The per-image maxima live in a fixed device array of PA_NOALLOC_MAX_IMAGES
  * ints inside this library (16 KiB held on every GPU that loads it until the
  * process exits); n_images > PA_NOALLOC_MAX_IMAGES returns PA_EINVAL.  The
  * first call on a device looks up that array's device address (once per
- * device), so make the first call before any stream capture.  Every call
+ * device and CUDA context: a new context on the device, e.g. after
+ * cudaDeviceReset, is looked up again on its first call), so make the first
+ * call before any stream capture.  Every call
  * reuses the same array and clears the slots it needs on cuda_stream before
  * use: calls whose work overlaps on the GPU (other streams, other threads)
  * race on it and must be serialised by the caller.  Asynchronous on

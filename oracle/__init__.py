@@ -15,6 +15,9 @@ Parity status per function (see the pins in ``tests/test_oracle_*.py``):
 * point-absorber peak                  pinned (true pixel, symmetry)
 * FFT                                  pinned (O(M^2) DFT, analytic cosine)
 * Hilbert envelope                     pinned (constant envelope of a cosine)
+* depth-to-frequency mapping           pinned (hand-worked bin frequencies and
+                                        Nyquist clip, an RF tone of known
+                                        temporal frequency through the whole path)
 * band-pass parameters                 parity unpinned (the paper gives no band)
 * log compression                      pinned (closed form)
 """

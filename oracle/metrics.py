@@ -1,4 +1,4 @@
-"""Image-quality metrics of Section 4, written out plainly in numpy FP64.
+"""Image-quality metrics of Section 3, written out plainly in numpy FP64.
 
 TEST INFRASTRUCTURE ONLY (the same rule as the rest of ``oracle/``): only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -15,7 +15,7 @@ TEST INFRASTRUCTURE ONLY (the same rule as the rest of ``oracle/``): only
   (reading).  The bin of a value is an integer decided in floating point, so
   it is taken in FP32 exactly as the GPU takes it: floor((v * 256) / vmax),
   clamped to [0, 255], values <= 0 in bin 0.
-* FWHM (lateral, Section 4's main-lobe width): on the image row of the
+* FWHM (lateral, the main-lobe width of Section 3): on the image row of the
   target maximum, walk out from the maximum while values stay >= half of it;
   each crossing is linearly interpolated between the last pixel >= half and
   the first pixel below; NaN if a side reaches the image edge.

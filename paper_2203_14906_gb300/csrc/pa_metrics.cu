@@ -1,4 +1,4 @@
-// pa_metrics.cu -- image-quality metrics of Section 4 (SNR Eq. 10, CR
+// pa_metrics.cu -- image-quality metrics of Section 3 (SNR Eq. 10, CR
 // Eq. 11, gCNR Eq. 12, lateral FWHM) on device-resident images.
 //
 // Work is split into "slots": one slot is one region (target or background)

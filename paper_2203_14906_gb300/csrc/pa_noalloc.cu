@@ -12,6 +12,8 @@
 // a device, so the call needs only the caller's input and output buffers.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "pa_internal.cuh"
 #include "pa_logdb.cuh"
 
@@ -24,7 +26,29 @@ static __device__ __align__(256) int g_noalloc_max[PA_NOALLOC_MAX_IMAGES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Device address of the array, per device, with the context it was looked up
+// in: a context created later on the same device (after cudaDeviceReset, or
+// one the caller made current) loads the library's module afresh, so the
+// address is looked up again there.
 int* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The current driver context (cuCtxGetCurrent, reached through the runtime
+// so that the library needs no link against the driver); null if unknown.
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 // Largest value of each image (negative inputs count as zero).
 __global__ void k_noalloc_image_max(const float* env, long long elems, int* slots) {
@@ -75,19 +99,23 @@ extern "C" pa_status pa_log_compress_noalloc(const float* env_dev, int32_t n_ima
     return noalloc_fail(PA_ECUDA, "pa_log_compress_noalloc: no current CUDA device");
   int* slots = nullptr;
   {
-    // One-time set-up per device: the host-side name of the array is not a
-    // device address, so ask the runtime for the address on this device.
+    // One-time set-up per device (and context): the host-side name of the
+    // array is not a device address, so ask the runtime for the address on
+    // this device, with the device current.
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_max);
       if (e != cudaSuccess || !p)
         return noalloc_fail(PA_ECUDA, "pa_log_compress_noalloc: cudaGetSymbolAddress failed");
       g_scratch_addr[dev] = static_cast<int*>(p);
+      g_scratch_ctx[dev] = current_context();  // the lookup may have created it
     }
     slots = g_scratch_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // as in pa_plan_desc: a range that is not positive (or NaN) means 60 dB
   const float dr = dyn_range_db > 0.f ? dyn_range_db : 60.f;
   // The array keeps the previous call's maxima: clear the slots this call uses.
   if (cudaMemsetAsync(slots, 0, (size_t)n_images * sizeof(int), st) != cudaSuccess)

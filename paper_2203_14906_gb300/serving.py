@@ -75,8 +75,8 @@ class Server:
     """Requests in, images out; batching and admission happen natively."""
 
     def __init__(self, budget_bytes: int, slots: int = 4, max_batch: int = 8,
-                 max_plans: int = 512, stages: int = PA_STAGE_LOG):
-        self._L = load()
+                 max_plans: int = 512, stages: int = PA_STAGE_LOG, checked: bool = False):
+        self._L = load(checked)
         _bind(self._L)
         self.cfg = ServerConfig(int(budget_bytes), int(slots), int(max_batch), int(max_plans),
                                 int(stages))

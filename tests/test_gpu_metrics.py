@@ -1,4 +1,4 @@
-"""Image-quality metrics (Section 4, Eqs. 10-12) on the GPU vs the oracle.
+"""Image-quality metrics (Section 3, Eqs. 10-12) on the GPU vs the oracle.
 
 Both sides read the same FP32 images (the GPU's own envelope output, copied
 to the host for the oracle), so pixel counts, peak positions and histogram
@@ -129,7 +129,7 @@ def test_many_images_and_pairs_across_launch_chunks():
 
 
 def test_fwhm_falls_with_order_through_the_gpu_path():
-    """Section 4's claim on GPU-beamformed images of a point absorber (odd
+    """Section 3's claim on GPU-beamformed images of a point absorber (odd
     orders in the fundamental band, even orders in the harmonic band)."""
     wl = synth.workload("cfg1", nx=257, nz=256, noise_frac=0.0, x0_m=-6.425e-3, x1_m=6.425e-3)
     l0 = 160

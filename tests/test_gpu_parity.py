@@ -496,3 +496,20 @@ def test_graph_cache_beyond_its_bound():
         for n in list(range(1, 41)) + [3, 17, 40]:
             out = pa.beamform(plan, rf[:n].contiguous(), 7)
             assert torch.equal(out, ref[:n]), n
+
+
+@pytest.mark.parametrize("b", [45, 77, 6])
+def test_tone_through_the_gpu_post_filter(b):
+    """The pinned one-element tone: an RF tone of known temporal frequency
+    lands on its depth bin and the GPU band-pass keeps or removes it as the
+    oracle does (in band: envelope 1; out of band: 0)."""
+    from test_oracle_post import _post_gold, tone_case
+
+    case = {c["b"]: c for c in _post_gold()["tone"]["cases"]}[b]
+    wl, rf = tone_case(b)
+    out, info, deq = run_gpu(wl, rf[None], 1, outputs=1, stages=3)
+    assert info["device_error_flags"] == 0
+    env = out[0, 1, 0, 0]
+    assert np.allclose(env, case["odd_env"], rtol=0, atol=1e-4)
+    assert_parity(compare(out, oracle_frames(wl, deq, 1), outputs=1, stages=3), TOL32,
+                  what=f"tone bin {b}")

@@ -1,4 +1,4 @@
-"""Pins for the oracle's image-quality metrics (Section 4, Eqs. 10-12).
+"""Pins for the oracle's image-quality metrics (Section 3, Eqs. 10-12).
 
 * SNR and CR closed forms on a constructed image: a constant target and a
   background of two interleaved levels (mean 2, population deviation 1).
@@ -8,7 +8,7 @@
   overlaps, and two Gaussian samples reach 1 - OVL of the normal densities.
 * FWHM: a triangular lobe (linear between pixels, so the interpolated
   crossing is exact), a Gaussian lobe (2 sqrt(2 ln 2) sigma), NaN at the edge.
-* Section 4's qualitative claim on a point absorber: the lateral FWHM falls
+* Section 3's qualitative claim on a point absorber: the lateral FWHM falls
   as the order grows (DAS > DMAS-3 > DMAS-5 and DMAS > DMAS-4).
 """
 
@@ -100,7 +100,7 @@ def test_fwhm_gaussian_and_edge():
 
 
 def test_fwhm_falls_with_order_on_a_point_absorber():
-    """Section 4: more correlated terms give a narrower main lobe.  Odd orders
+    """Section 3: more correlated terms give a narrower main lobe.  Odd orders
     keep the fundamental band and even orders the second-harmonic band after
     the post filter, so widths are compared within each family (and every
     higher order against DAS)."""

@@ -4,7 +4,10 @@ band-pass mask and log compression.
 The band-pass *parameters* are parity unpinned (the paper names no band);
 what is pinned is the FFT (against its O(M^2) DFT and numpy.fft), the
 analytic-signal mask, the envelope of an in-band cosine (constant, equal
-to its amplitude), removal of DC, and the closed form of the log stage.
+to its amplitude), removal of DC, the closed form of the log stage, and the
+mapping of depth bins to temporal frequency under one-way propagation
+(hand-worked bins and Nyquist clip; an RF tone of known frequency carried
+through the beamformer keeps or loses its envelope as its frequency says).
 """
 
 import json
@@ -116,3 +119,63 @@ def test_log_closed_form():
     out = oracle.log_image(np.array(g["env"]), g["dyn_range_db"])
     assert np.allclose(out, g["expected"], atol=1e-12)
     assert np.all(oracle.log_image(np.zeros(5), 60.0) == -60.0)
+
+
+# ---- depth-to-frequency mapping (reading of the Section 3 band-pass) ------
+# Pinned from outside the oracle: hand-worked bin frequencies and masks, and
+# an RF tone of known temporal frequency carried through the beamformer to
+# its depth bin.  A mapping off by a factor of two (two-way c / 2, or 2 c)
+# fails both the literal values and the tone outcomes.
+
+def _post_gold():
+    return json.load(open(os.path.join(GOLD, "post_worked.json")))
+
+
+def test_bin_hz_hand_worked():
+    for case in _post_gold()["bin_hz"]:
+        wl = synth.workload("cfg1", nz=case["nz"], z0_m=case["z0_m"], z1_m=case["z1_m"],
+                            c_m_s=case["c_m_s"])
+        got = oracle.bin_hz(wl, case["m"], case["b"])
+        assert got == pytest.approx(case["hz"], rel=1e-12), case["workload"]
+
+
+def test_nyquist_clip_odd_order_cfg1():
+    """cfg1's axial Nyquist rate (4.93 MHz) lies inside the odd band
+    [2.5, 7.5] MHz: the band is clipped, not reduced to DC removal."""
+    g = _post_gold()["cfg1_odd_mask"]
+    wl = synth.workload("cfg1")
+    h, dc_only = oracle.post_mask(wl, False)
+    assert h.size == 128
+    assert dc_only == g["dc_only"]
+    assert np.all(h[: g["zero_bins_upto"] + 1] == 0.0)
+    r0, r1 = g["rolloff_bins"]
+    assert np.all((h[r0 : r1 + 1] > 0.0) & (h[r0 : r1 + 1] < 2.0))
+    b0, b1 = g["band_bins"]
+    assert np.all(h[b0 : b1 + 1] == 2.0)
+    assert h[64] == g["nyquist_bin_weight"]
+    assert np.all(h[65:] == 0.0)
+    assert h[g["b20"]["b"]] == pytest.approx(g["b20"]["h"], abs=1e-12)
+
+
+def tone_case(b):
+    """(workload, RF frame) of the one-element tone pin at depth bin b."""
+    g = _post_gold()["tone"]
+    wl = dict(g["geometry"], name="tone", interp="linear")
+    n = np.arange(wl["n_samples"])
+    f = b * wl["fs_hz"] / wl["nz"]
+    rf = np.cos(2 * np.pi * f * n / wl["fs_hz"] + g["phase"])[None, :]
+    return wl, rf
+
+
+@pytest.mark.parametrize("case", _post_gold()["tone"]["cases"], ids=lambda c: f"bin{c['b']}")
+def test_tone_passes_or_is_blocked_by_its_temporal_frequency(case):
+    wl, rf = tone_case(case["b"])
+    out = oracle.frame(wl, rf, order_k=1)
+    raw = out["raw"]["das"][0]
+    # the DAS column is the tone sampled at tau = l + 1 (exact delays)
+    want_raw = rf[0, 1 : wl["nz"] + 1]
+    assert np.allclose(raw, want_raw, rtol=0, atol=1e-9)
+    env = out["env"]["das"][0]
+    assert np.allclose(env, case["odd_env"], rtol=0, atol=1e-9)
+    h_even, _ = oracle.post_mask(wl, True)
+    assert np.allclose(oracle.envelope(raw, h_even), case["even_env"], rtol=0, atol=1e-9)
