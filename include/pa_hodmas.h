@@ -63,6 +63,24 @@ typedef enum { PA_RF_F32 = 0, PA_RF_BF16 = 1, PA_RF_F16 = 2 } pa_rf_dtype;
  * iff 0 <= round(tau) <= Ns-1, rounding halves up). */
 typedef enum { PA_INTERP_LINEAR = 0, PA_INTERP_NEAREST = 1 } pa_interp;
 
+/* Form of the resident delay / apodisation table (Section 5 precomputes the
+ * delay of every pixel and element into GPU memory).
+ *   LATTICE  the delay depends on the pixel and the element only through
+ *            their lateral offset and the depth; when the element pitch is
+ *            an integer multiple m (1..32) of the lateral pixel pitch those
+ *            offsets lie on a lattice of about nx + m N values, and one
+ *            table row per lattice offset serves every pair on it (a few MB,
+ *            resident in L2).
+ *   FULL     one entry per pixel and element (nx x N x nz; 8 bytes, plus 4
+ *            with apodisation): any lateral grid, finer or coarser than the
+ *            pitch or incommensurate with it.
+ *   AUTO     LATTICE when the grid allows it, else FULL.
+ * Both forms hold the same FP64-computed delays, so images agree to FP32
+ * rounding of the sums. */
+typedef enum { PA_TABLE_AUTO = 0, PA_TABLE_LATTICE = 1, PA_TABLE_FULL = 2 } pa_delay_table;
+/* Largest FULL table pa_plan builds (bytes). */
+#define PA_FULL_TABLE_MAX_BYTES ((size_t)16 << 30)
+
 /* Output images (bit mask).  Planes of one frame are ordered DAS, DMAS,
  * HODMAS, keeping only the requested ones. */
 enum { PA_OUT_DAS = 1u, PA_OUT_DMAS = 2u, PA_OUT_HODMAS = 4u };
@@ -78,8 +96,9 @@ typedef struct {
   double t0_s;           /* time of RF sample 0 after the laser shot        */
   int32_t n_samples;     /* Ns >= 2 samples per channel                     */
   int32_t nx, nz;        /* image grid >= 1                                 */
-  double x0_m, x1_m;     /* lateral extent, x1 > x0; (x1-x0)/nx must divide
-                            the pitch: pitch / dx = integer m in 1..32      */
+  double x0_m, x1_m;     /* lateral extent, x1 > x0 (any lateral pitch dx;
+                            pitch / dx an integer 1..32 allows the lattice
+                            delay table)                                    */
   double z0_m, z1_m;     /* depth extent, 0 <= z0 < z1                      */
   int32_t order_k;       /* 1..8; 1 = DAS only, 2 = DMAS                    */
   uint32_t outputs;      /* PA_OUT_* mask, non-zero                         */
@@ -94,13 +113,15 @@ typedef struct {
   int32_t compensated;   /* 1: Kahan-compensated FP32 power sums (totals
                             and compensation terms kept in tensor memory) */
   pa_interp interp;      /* sampling of the delayed signal                  */
+  pa_delay_table delay_table; /* table form; PA_TABLE_AUTO picks            */
 } pa_plan_desc;
 
 typedef struct pa_plan_s* pa_plan_t;
 
 /* Read-only facts about a plan (for tests, benchmarks and admission). */
 typedef struct {
-  int32_t lattice_m;          /* pitch / lateral pixel pitch               */
+  int32_t lattice_m;          /* pitch / lateral pixel pitch (lattice table;
+                                 1 with the full table)                    */
   int32_t tile_x, tile_z;     /* pixel tile of one thread block            */
   int32_t window;             /* RF samples staged per channel per tile    */
   int32_t n_tiles;            /* tiles per frame                           */
@@ -131,6 +152,8 @@ typedef struct {
                                  block allocates for the Kahan totals of
                                  compensated sums (0: plain sums); resident
                                  blocks per SM x tmem_columns <= 512       */
+  int32_t delay_table;        /* PA_TABLE_LATTICE or PA_TABLE_FULL         */
+  size_t table_bytes;         /* bytes of the delay (+ apodisation) table  */
 } pa_plan_info;
 
 /*
@@ -143,8 +166,9 @@ typedef struct {
  * once before returning.  On success *out owns all device memory it
  * allocated until pa_destroy.
  * Errors: PA_EINVAL (null pointer, sizes, order outside 1..8, N < k, z0 < 0,
- * non-integer pitch / dx), PA_EUNSUPPORTED (lattice m > 32, RF window too
- * large for shared memory), PA_ENOMEM, PA_ECUDA.
+ * PA_TABLE_LATTICE asked for a grid whose pitch / dx is not an integer in
+ * 1..32), PA_EUNSUPPORTED (full table above PA_FULL_TABLE_MAX_BYTES, RF
+ * window too large for shared memory), PA_ENOMEM, PA_ECUDA.
  * Environment, read here (for measurements and tests; results do not depend
  * on the first three): PA_STAGING=tma|loads picks the RF staging path (TMA
  * boxes need Ns to be a multiple of the window alignment), PA_CHUNK_STEPS=n
@@ -482,7 +506,7 @@ const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);
 /* ABI version (major * 100 + minor). */
-int32_t pa_version(void);  /* 103: host-path chunk schedules */
+int32_t pa_version(void);  /* 104: full per-pixel delay table */
 
 #ifdef __cplusplus
 }

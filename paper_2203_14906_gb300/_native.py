@@ -22,6 +22,8 @@ PA_OUT_DAS, PA_OUT_DMAS, PA_OUT_HODMAS = 1, 2, 4
 PA_STAGE_RAW, PA_STAGE_ENV, PA_STAGE_LOG = 1, 2, 4
 PA_INTERP_LINEAR, PA_INTERP_NEAREST = 0, 1
 INTERPS = {"linear": PA_INTERP_LINEAR, "nearest": PA_INTERP_NEAREST}
+PA_TABLE_AUTO, PA_TABLE_LATTICE, PA_TABLE_FULL = 0, 1, 2
+DELAY_TABLES = {"auto": PA_TABLE_AUTO, "lattice": PA_TABLE_LATTICE, "full": PA_TABLE_FULL}
 
 RF_DTYPES = {"f32": PA_RF_F32, "bf16": PA_RF_BF16, "f16": PA_RF_F16}
 
@@ -72,6 +74,7 @@ class PlanDesc(ctypes.Structure):
         ("dyn_range_db", ctypes.c_double),
         ("compensated", ctypes.c_int32),
         ("interp", ctypes.c_int32),
+        ("delay_table", ctypes.c_int32),
     ]
 
 
@@ -112,6 +115,8 @@ class PlanInfo(ctypes.Structure):
         ("chunk_steps", ctypes.c_int32),
         ("lane_rows", ctypes.c_int32),
         ("tmem_columns", ctypes.c_int32),
+        ("delay_table", ctypes.c_int32),
+        ("table_bytes", ctypes.c_size_t),
     ]
 
     def as_dict(self):
@@ -279,6 +284,7 @@ def make_desc(wl: dict, order_k=None, outputs=7, rf_dtype=None, max_batch=1,
         dyn_range_db=float(wl.get("dyn_range_db", 60.0)),
         compensated=int(wl.get("compensated", 0) if compensated is None else compensated),
         interp=INTERPS[wl.get("interp", "linear")],
+        delay_table=DELAY_TABLES[wl.get("delay_table", "auto")],
     )
 
 

@@ -2,6 +2,11 @@
 // power-sum kernel with an FP64 e_k epilogue (Sections 2.1-2.3: Eq. 1 DAS,
 // Eq. 3 real-time DMAS, Eqs. 7-9 O(N) DMAS-k).
 //
+// Delay tables: LATTICE (one entry per lattice offset and depth, shared by
+// the kC pairs of a thread at one channel step, see below) or FULL (one
+// entry per pixel and element, Section 5's precomputed delays for any
+// grid); the FULL kernel reads kC entries per step, one per pair.
+//
 // Work decomposition (one persistent CTA loop over work items):
 //   item   = (pixel tile, residue group, frame), taken from an atomic counter
 //   tile   = tile_x columns x 32 depth rows; lane = depth row
@@ -474,7 +479,7 @@ struct MinBlocks {
   static constexpr int value = K >= 6 ? 2 : (K <= PA_MINB4_MAX_K && !COMP ? 4 : 3);
 };
 
-template <int K, bool APOD, bool COMP>
+template <int K, bool APOD, bool COMP, bool FULL>
 __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     k_bf_fused(const __grid_constant__ BfParams p) {
   constexpr int NA = NAcc<K>::value;
@@ -554,11 +559,15 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     }
     int fold = 0;
 
-    // Table rows of this thread: row t(u) = jt - dmin - m u at depth z.
+    // Table rows of this thread.  LATTICE: row t(u) = jt - dmin - m u at
+    // depth z.  FULL: the entry of pixel c (column jt + c) and channel
+    // u + c at depth z sits at fcol + (u - u0) nzp + c fcst.
     const int2* tcol = p.table + z;
     const float* wcol = APOD ? p.wtab + z : nullptr;
     const int row_u0 = jt - p.dmin;
     const int mstride = p.m * p.table_stride;
+    const size_t fcst = (size_t)(p.nv + 1) * p.table_stride;
+    const size_t fbase0 = (size_t)jt * p.nv * p.table_stride + z;
 
     int lo_next = 0;  // window start of my channel in the next chunk to issue
     if (p.use_tma && vk.x < vk.y) {
@@ -622,6 +631,79 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       int u = max(cu0, ur.x);
       const int u_end = min(cu0 + p.nc, ur.y);
       if (u >= u_end) continue;
+
+      if constexpr (FULL) {
+        // Entries (n0, a) [and weights] of the kC pairs of step uu.
+        auto load_step = [&](int2 (&e)[kC], float (&w)[kC], int uu) {
+          const size_t o = fbase0 + (size_t)(uu - p.u0) * p.table_stride;
+#ifdef PA_CHECK_BOUNDS
+          if (o + (kC - 1) * fcst >= (size_t)p.ndrows * p.table_stride) atomicOr(p.err, 1);
+#endif
+#pragma unroll
+          for (int c = 0; c < kC; ++c) {
+            e[c] = __ldg(p.table + o + c * fcst);
+            if constexpr (APOD) w[c] = __ldg(p.wtab + o + c * fcst);
+          }
+        };
+        // kC steps from uu; the entries of the next step are loaded while
+        // the current one is evaluated (the last step of the chunk reloads
+        // its own entries instead of reading past the chunk).
+        auto fblock = [&](auto near_tag, int2 (&e)[kC], float (&w)[kC], int uu) {
+          constexpr bool NEAR = decltype(near_tag)::value;
+          int cb[2 * kC];
+          {
+            const int4* cbv = reinterpret_cast<const int4*>(s_cb + (uu - cu0));
+            const int4 c0 = cbv[0], c1 = cbv[1];
+            cb[0] = c0.x; cb[1] = c0.y; cb[2] = c0.z; cb[3] = c0.w;
+            cb[4] = c1.x; cb[5] = c1.y; cb[6] = c1.z; cb[7] = c1.w;
+          }
+#pragma unroll
+          for (int tt = 0; tt < kC; ++tt) {
+            int2 e2[kC];
+            float w2[kC];
+            load_step(e2, w2, min(uu + tt + 1, u_end - 1));
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+              int addr = cb[tt + c] + e[c].x;
+#ifdef PA_CHECK_BOUNDS
+              if (addr < pairs_off || addr > smem_hi) {
+                atomicOr(p.err, 2);
+                addr = pairs_off;
+              }
+#endif
+              float s;
+              if constexpr (NEAR) {
+                asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(addr));
+              } else {
+                float2 r;
+                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
+                s = fmaf(__int_as_float(e[c].y), r.y, r.x);
+              }
+              if constexpr (APOD) s *= w[c];
+              pair_update<K>(acc[c], s);
+            }
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+              e[c] = e2[c];
+              if constexpr (APOD) w[c] = w2[c];
+            }
+          }
+          if constexpr (COMP) {
+            if (++fold == kFoldBlocks) {
+              kahan_fold_tmem<NA>(acc, tmem);
+              fold = 0;
+            }
+          }
+        };
+        int2 e[kC];
+        float w[kC];
+        load_step(e, w, u);
+        for (; u < u_end; u += kC) {
+          if (p.nearest) fblock(std::true_type{}, e, w, u);
+          else fblock(std::false_type{}, e, w, u);
+        }
+        continue;
+      } else {
 
       // Table entries (n0, a) [and weight] of the kC steps starting at uu.
       auto load_entries = [&](int2 (&ee)[kC], float (&ww)[kC], int uu) {
@@ -696,6 +778,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         if (p.nearest) block(std::true_type{}, eb, wb, u + kC);
         else block(std::false_type{}, eb, wb, u + kC);
       }
+      }  // LATTICE
     }
     if (timed_out) break;
     if constexpr (TSUM) kahan_fold_tmem<NA>(acc, tmem);
@@ -750,26 +833,31 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
 // One translation unit per order: launch and occupancy wrappers.
 #define PA_DEFINE_ORDER(K)                                                      \
   namespace pa {                                                                \
-  static void (*pick_k##K(bool apod, bool comp))(BfParams) {                    \
-    if (apod) return comp ? k_bf_fused<K, true, true> : k_bf_fused<K, true, false>; \
-    return comp ? k_bf_fused<K, false, true> : k_bf_fused<K, false, false>;     \
+  template <bool FULL>                                                          \
+  static void (*pick_form_k##K(bool apod, bool comp))(BfParams) {               \
+    if (apod)                                                                   \
+      return comp ? k_bf_fused<K, true, true, FULL> : k_bf_fused<K, true, false, FULL>; \
+    return comp ? k_bf_fused<K, false, true, FULL> : k_bf_fused<K, false, false, FULL>; \
   }                                                                             \
-  cudaError_t bf_launch_k##K(bool apod, bool comp, const BfParams& p, int grid, \
-                             int block, size_t smem, cudaStream_t s) {          \
-    void (*f)(BfParams) = pick_k##K(apod, comp);                                \
+  static void (*pick_k##K(bool apod, bool comp, bool full))(BfParams) {         \
+    return full ? pick_form_k##K<true>(apod, comp) : pick_form_k##K<false>(apod, comp); \
+  }                                                                             \
+  cudaError_t bf_launch_k##K(bool apod, bool comp, bool full, const BfParams& p, \
+                             int grid, int block, size_t smem, cudaStream_t s) { \
+    void (*f)(BfParams) = pick_k##K(apod, comp, full);                          \
     f<<<grid, block, smem, s>>>(p);                                             \
     return cudaGetLastError();                                                  \
   }                                                                             \
-  cudaError_t bf_occupancy_k##K(bool apod, bool comp, int block, size_t smem,   \
-                                int* blocks_per_sm) {                           \
-    void (*f)(BfParams) = pick_k##K(apod, comp);                                \
+  cudaError_t bf_occupancy_k##K(bool apod, bool comp, bool full, int block,     \
+                                size_t smem, int* blocks_per_sm) {              \
+    void (*f)(BfParams) = pick_k##K(apod, comp, full);                          \
     cudaError_t e = cudaFuncSetAttribute(                                       \
         f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);            \
     if (e != cudaSuccess) return e;                                             \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f,      \
                                                          block, smem);          \
   }                                                                             \
-  const void* bf_func_k##K(bool apod, bool comp) {                              \
-    return reinterpret_cast<const void*>(pick_k##K(apod, comp));                \
+  const void* bf_func_k##K(bool apod, bool comp, bool full) {                   \
+    return reinterpret_cast<const void*>(pick_k##K(apod, comp, full));          \
   }                                                                             \
   }

@@ -76,7 +76,9 @@ struct BfParams {  // aligned as CUtensorMap requires
   int tmem_cols;          // TMEM columns a block allocates (compensated sums), else 0
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
-  const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}
+  const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}; rows are
+                          // lattice offsets, or (column, virtual channel) pairs
+                          // of the full table
   const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)
   int table_stride;       // nz_pad
   const int4* items;      // [n_tiles * ngroups] {tile_id, grp, tx, tz}, deepest first
@@ -141,7 +143,7 @@ struct LaunchSpec {
   size_t smem = 0;
 };
 
-const void* bf_func(int order, bool apod, bool comp);
+const void* bf_func(int order, bool apod, bool comp, bool full);
 void post_spec(const PostParams& p, LaunchSpec* s);
 // Radix of the first FFT pass of the in-place post kernel (the passes after
 // it are radix 8, then one radix-4 or radix-2 pass for the remainder); the
@@ -157,18 +159,18 @@ int post_team_warps(int m);  // warps per team (column pair) of the post kernel
 void log_spec(const LogParams& p, int num_sms, LaunchSpec* s);
 
 // Launchers (one translation unit per order keeps the builds parallel).
-cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p,
+cudaError_t bf_launch(int order, bool apod, bool comp, bool full, const BfParams& p,
                       int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t bf_occupancy(int order, bool apod, bool comp, int block,
+cudaError_t bf_occupancy(int order, bool apod, bool comp, bool full, int block,
                          size_t smem, int* blocks_per_sm);
 
 #define PA_DECLARE_ORDER(K)                                                 \
-  cudaError_t bf_launch_k##K(bool apod, bool comp, const BfParams& p,       \
-                             int grid, int block, size_t smem,              \
-                             cudaStream_t s);                               \
-  cudaError_t bf_occupancy_k##K(bool apod, bool comp, int block,            \
+  cudaError_t bf_launch_k##K(bool apod, bool comp, bool full,               \
+                             const BfParams& p, int grid, int block,        \
+                             size_t smem, cudaStream_t s);                  \
+  cudaError_t bf_occupancy_k##K(bool apod, bool comp, bool full, int block, \
                                 size_t smem, int* blocks_per_sm);           \
-  const void* bf_func_k##K(bool apod, bool comp);
+  const void* bf_func_k##K(bool apod, bool comp, bool full);
 PA_DECLARE_ORDER(1)
 PA_DECLARE_ORDER(2)
 PA_DECLARE_ORDER(3)

@@ -63,6 +63,7 @@ struct pa_plan_s {
   int device = 0, num_sms = 0;
   int K = 1;
   bool apod = false, comp = false;
+  bool full = false;  // per-pixel delay table (PA_TABLE_FULL) instead of the lattice
   // tiling
   int m = 1, R = 1, slots = 1, warps = 1, ngroups = 1, threads = 32;
   int tile_x = 0, tile_z = 32, nxt = 0, nzt = 0, n_tiles = 0, nx_pad = 0, nz_pad = 0;
@@ -168,18 +169,18 @@ struct TableGeom {
   int ndrows, nzp, dmin, ns, nearest;
   double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
   double dx, z0, dz, fs, c, t0, fnum;
+  // full table: element i = v + u0 of N at x_i = (i - (N-1)/2) pitch
+  double x0, pitch;
+  int n_elem, u0, nv;
 };
 
-// Delay (and apodisation) for every lattice offset d = j - m i and depth row.
-// One-way time of flight in samples, tau = fs (r / c - t0), stored as the
-// integer sample n0 = floor(tau) (pre-scaled by 8, the byte stride of an
-// interpolation pair) and the FP32 fraction a = tau - n0.
-__global__ void k_table(TableGeom g, int2* table, float* wtab) {
-  const int z = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = blockIdx.y;
-  if (z >= g.nzp || row >= g.ndrows) return;
-  const double dxv = g.x_const + ((double)(g.dmin + row) + 0.5) * g.dx;
-  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
+// One table entry: the one-way time of flight in samples from a pixel at
+// lateral offset dxv from the element and depth zp, tau = fs (r / c - t0),
+// stored as the integer sample n0 = floor(tau) (pre-scaled by 8, the byte
+// stride of an interpolation pair) and the FP32 fraction a = tau - n0; and
+// the apodisation weight.
+__device__ void table_entry(const TableGeom& g, double dxv, double zp, size_t ti, int2* table,
+                            float* wtab) {
   const double tau = g.fs * (sqrt(dxv * dxv + zp * zp) / g.c - g.t0);
   // linear: n0 = floor(tau), a = tau - n0; nearest (Eq. 1): n0 = round(tau), a = 0
   double fl = g.nearest ? floor(tau + 0.5) : floor(tau);
@@ -196,7 +197,6 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   // n0 = Ns-1 already give 0 and r[Ns-1], so no remapping is needed.)
   if (!g.nearest && n0 == -1) n0 = -2;
   if (!g.nearest && n0 == g.ns - 1) n0 = g.ns;
-  const size_t ti = table_index(row, z, g.nzp);
   table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
   if (wtab) {
     float w = 0.f;
@@ -209,9 +209,39 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   }
 }
 
+// Lattice table: every lattice offset d = j - m i and depth row.
+__global__ void k_table(TableGeom g, int2* table, float* wtab) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (z >= g.nzp || row >= g.ndrows) return;
+  const double dxv = g.x_const + ((double)(g.dmin + row) + 0.5) * g.dx;
+  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
+  table_entry(g, dxv, zp, table_index(row, z, g.nzp), table, wtab);
+}
+
+// Full table: every (pixel column j, virtual channel v) pair and depth row,
+// row j * nv + v; the lateral offset is x_j - x_i with both positions
+// computed from the grid and the array as they are defined.
+__global__ void k_table_full(TableGeom g, int2* table, float* wtab) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y, j = blockIdx.z;
+  if (z >= g.nzp) return;
+  const double xp = g.x0 + ((double)j + 0.5) * g.dx;
+  const double xi = ((double)(v + g.u0) - 0.5 * (double)(g.n_elem - 1)) * g.pitch;
+  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
+  table_entry(g, xp - xi, zp, table_index(j * g.nv + v, z, g.nzp), table, wtab);
+}
+
 struct TileGeom {
   int nxt, nzt, tile_x, tile_z, m, dmin, nzp, nv, u0, ndrows;
+  int full;  // 1: rows are (column, virtual channel) pairs, j * nv + v
 };
+
+// Table row of pixel column j and virtual channel v (lattice: offset
+// d = j - m i; full: j * nv + v).
+__device__ __forceinline__ int tile_row(const TileGeom& g, int j, int v) {
+  return g.full ? j * g.nv + v : j - g.m * (v + g.u0) - g.dmin;
+}
 
 // First staged sample (rounded down to a multiple of 4) and window width of
 // every (tile, virtual channel).  The delay grows with depth for z > 0, so the
@@ -222,12 +252,10 @@ __global__ void k_windows(TileGeom g, int lo_align, const int2* table, int* lo, 
   const int tile = blockIdx.y;
   if (v >= g.nv) return;
   const int tx = tile % g.nxt, tz = tile / g.nxt;
-  const int i = v + g.u0;
   const int zf = tz * g.tile_z, zl = zf + g.tile_z - 1;
   int mn = 0x7fffffff, mx = -0x7fffffff;
   for (int jj = 0; jj < g.tile_x; ++jj) {
-    const int d = tx * g.tile_x + jj - g.m * i;
-    const int row = d - g.dmin;
+    const int row = tile_row(g, tx * g.tile_x + jj, v);
     if (row < 0 || row >= g.ndrows) {
       atomicOr(err, 4);
       continue;
@@ -256,9 +284,15 @@ __global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wt
     const int zl = tz * g.tile_z + g.tile_z - 1;
     int ua = u1, ub = g.u0;
     for (int u = g.u0; u < u1; ++u) {
-      const int row = jt - g.m * u - g.dmin;
-      if (row < 0 || row >= g.ndrows) continue;
-      if (wtab[table_index(row, zl, g.nzp)] > 0.f) {
+      // lattice: the kC pixels of the slot share one entry at step u; full:
+      // pixel c (column jt + c) pairs with channel u + c
+      bool on = false;
+      for (int c = 0; c < (g.full ? kc : 1); ++c) {
+        const int row = tile_row(g, jt + c, u - g.u0 + c);
+        if (row < 0 || row >= g.ndrows) continue;
+        on |= wtab[table_index(row, zl, g.nzp)] > 0.f;
+      }
+      if (on) {
         ua = min(ua, u);
         ub = max(ub, u + 1);
       }
@@ -280,15 +314,15 @@ __global__ void k_zero_ints(int* p, int n) {
 }
 
 // Pairs with a non-zero apodisation weight (for the active-pair rate).
-__global__ void k_count_active(int nx, int nz, int n, int m, int dmin, int nzp,
-                               const float* wtab, unsigned long long* count) {
+__global__ void k_count_active(TileGeom g, int nx, int nz, int n, const float* wtab,
+                               unsigned long long* count) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   unsigned long long c = 0;
   if (z < nz) {
     for (int i = 0; i < n; ++i) {
-      const int row = j - m * i - dmin;
-      if (wtab[table_index(row, z, nzp)] > 0.f) ++c;
+      const int row = tile_row(g, j, i - g.u0);
+      if (wtab[table_index(row, z, g.nzp)] > 0.f) ++c;
     }
   }
   for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(0xffffffffu, c, s);
@@ -338,6 +372,16 @@ bool build_mask(const pa_plan_desc& d, bool even_order, int M, float* out) {
   return dc_only;
 }
 
+// pitch / lateral pixel pitch when it is an integer m in 1..32 (the lattice
+// table applies), else 0.
+int lattice_m(const pa_plan_desc& d) {
+  const double dx = (d.x1_m - d.x0_m) / d.nx;
+  const double mr = d.pitch_m / dx;
+  const double mi = std::round(mr);
+  if (mi < 1 || mi > 32 || std::fabs(mr - mi) > 1e-6 * mi) return 0;
+  return (int)mi;
+}
+
 pa_status validate(const pa_plan_desc* d) {
   if (!d) return fail(PA_EINVAL, "null descriptor");
   if (d->n_elem < 1) return fail(PA_EINVAL, "n_elem must be >= 1 (got %d)", d->n_elem);
@@ -365,15 +409,15 @@ pa_status validate(const pa_plan_desc* d) {
       return fail(PA_EINVAL, "f0_hz must be positive for the default band");
   }
   if (d->max_batch > 65535) return fail(PA_EINVAL, "max_batch must be <= 65535");
-  const double dx = (d->x1_m - d->x0_m) / d->nx;
-  const double mr = d->pitch_m / dx;
-  const double mi = std::round(mr);
-  if (mi < 1 || std::fabs(mr - mi) > 1e-6 * mi)
+  if (d->delay_table != PA_TABLE_AUTO && d->delay_table != PA_TABLE_LATTICE &&
+      d->delay_table != PA_TABLE_FULL)
+    return fail(PA_EINVAL, "delay_table %d invalid", (int)d->delay_table);
+  if (d->delay_table == PA_TABLE_LATTICE && lattice_m(*d) == 0)
     return fail(PA_EINVAL,
-                "pitch / lateral pixel pitch = %.9g is not a positive integer; choose x0, x1, "
-                "nx with (x1-x0)/nx = pitch/m",
-                mr);
-  if (mi > 32) return fail(PA_EUNSUPPORTED, "pitch / dx = %d > 32", (int)mi);
+                "pitch / lateral pixel pitch = %.9g is not an integer in 1..32: the lattice "
+                "delay table needs (x1-x0)/nx = pitch/m (PA_TABLE_AUTO or PA_TABLE_FULL take "
+                "any grid)",
+                d->pitch_m * d->nx / (d->x1_m - d->x0_m));
   return PA_OK;
 }
 
@@ -384,11 +428,24 @@ void configure(pa_plan_s* P) {
   P->apod = d.f_number > 0;
   P->comp = d.compensated != 0;
   const double dx = (d.x1_m - d.x0_m) / d.nx;
-  P->m = (int)std::lround(d.pitch_m / dx);
+  const int lm = lattice_m(d);
+  P->full = d.delay_table == PA_TABLE_FULL || (d.delay_table == PA_TABLE_AUTO && lm == 0);
+  // the full table pairs pixel c of a thread (column jt + c) with channel
+  // u + c; no entry is shared, so the columns of a thread are neighbours
+  P->m = P->full ? 1 : lm;
   // 32-column tiles halve the staged samples per pair; small images keep
   // 16-column tiles so that there are enough tiles to fill the GPU.
   const bool big = (int64_t)d.nx * d.nz >= 512 * 512;
   P->R = std::max(1, (big ? 8 : 4) / P->m);
+  if (P->full) {
+    // the RF window of a tile spans the delays over its lateral extent:
+    // keep tiles within ~3.2 mm laterally, in a power of two of column
+    // groups (whole warps of 8-row lane groups)
+    const int rmax = (int)std::floor(3.2e-3 / (kC * dx) + 1e-9);
+    int r = 1;
+    while (2 * r <= std::min(P->R, rmax)) r *= 2;
+    P->R = r;
+  }
   P->slots = P->m * P->R;
   int B = 1;
   for (int b = 1; b <= 8; ++b)
@@ -432,9 +489,14 @@ void configure(pa_plan_s* P) {
   P->u1 = P->u0 + steps;
   const int i_max = P->u1 - 1 + kC - 1;
   P->nv = i_max - P->u0 + 1;
-  P->dmin = -P->m * i_max;
-  const int dmax = P->nx_pad - 1 + P->m * (kC - 1);
-  P->ndrows = dmax - P->dmin + 1;
+  if (P->full) {  // rows: (pixel column, virtual channel) pairs
+    P->dmin = 0;
+    P->ndrows = P->nx_pad * P->nv;
+  } else {
+    P->dmin = -P->m * i_max;
+    const int dmax = P->nx_pad - 1 + P->m * (kC - 1);
+    P->ndrows = dmax - P->dmin + 1;
+  }
   P->M = 1;
   P->log2M = 0;
   while (P->M < d.nz) {
@@ -493,10 +555,10 @@ void configure(pa_plan_s* P) {
 // kernel that allocates tensor memory) and is capped so that the resident
 // blocks' TMEM columns fit the SM's 512.
 cudaError_t fused_blocks_per_sm(const pa_plan_s* P, size_t smem, int* n) {
-  cudaError_t e = bf_occupancy(P->K, P->apod, P->comp, P->threads, smem, n);
+  cudaError_t e = bf_occupancy(P->K, P->apod, P->comp, P->full, P->threads, smem, n);
   if (e != cudaSuccess || !P->tmem_cols) return e;
   cudaFuncAttributes a;
-  e = cudaFuncGetAttributes(&a, bf_func(P->K, P->apod, P->comp));
+  e = cudaFuncGetAttributes(&a, bf_func(P->K, P->apod, P->comp, P->full));
   if (e != cudaSuccess) return e;
   int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0, rsv = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -512,6 +574,20 @@ cudaError_t fused_blocks_per_sm(const pa_plan_s* P, size_t smem, int* n) {
   b = std::min(b, blk_sm);
   *n = std::max(0, std::min(b, kTmemColsPerSm / P->tmem_cols));
   return cudaSuccess;
+}
+
+// Bytes of the delay table and its apodisation weights.
+size_t delay_table_bytes(const pa_plan_s* P) {
+  return (size_t)P->ndrows * P->nz_pad * (sizeof(int2) + (P->apod ? sizeof(float) : 0));
+}
+
+pa_status check_table_size(const pa_plan_s* P) {
+  if (P->full && delay_table_bytes(P) > PA_FULL_TABLE_MAX_BYTES)
+    return fail(PA_EUNSUPPORTED,
+                "the full delay table of %d x %d x %d entries (%zu bytes) exceeds "
+                "PA_FULL_TABLE_MAX_BYTES",
+                P->nx_pad, P->nv, P->nz_pad, delay_table_bytes(P));
+  return PA_OK;
 }
 
 size_t table_bytes(const pa_plan_s* P) {
@@ -603,6 +679,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
 
   pa_status s;
   const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
+  if ((s = check_table_size(P)) != PA_OK) return s;
   if ((s = dalloc(P, &P->table, tab_n)) != PA_OK) return s;
   if (P->apod && (s = dalloc(P, &P->wtab, tab_n)) != PA_OK) return s;
   if ((s = dalloc(P, &P->items, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
@@ -637,11 +714,19 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   tg.c = d.c_m_s;
   tg.t0 = d.t0_s;
   tg.fnum = d.f_number;
-  {
+  tg.x0 = d.x0_m;
+  tg.pitch = d.pitch_m;
+  tg.n_elem = d.n_elem;
+  tg.u0 = P->u0;
+  tg.nv = P->nv;
+  if (P->full) {
+    dim3 grid((P->nz_pad + 127) / 128, P->nv, P->nx_pad);
+    k_table_full<<<grid, 128, 0, st>>>(tg, P->table, P->wtab);
+  } else {
     dim3 grid((P->nz_pad + 127) / 128, P->ndrows);
     k_table<<<grid, 128, 0, st>>>(tg, P->table, P->wtab);
-    PA_CUDA(cudaGetLastError());
   }
+  PA_CUDA(cudaGetLastError());
 
   // per-tile windows and warp ranges
   TileGeom g;
@@ -655,6 +740,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   g.nv = P->nv;
   g.u0 = P->u0;
   g.ndrows = P->ndrows;
+  g.full = P->full ? 1 : 0;
   int* wmax = P->scratch[0] + 2;  // borrowed before first use as image maxima
   {
     dim3 grid((P->nv + 127) / 128, P->n_tiles);
@@ -671,8 +757,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
     PA_CUDA(cudaMalloc(&cnt, sizeof(unsigned long long)));
     PA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
     dim3 grid((d.nz + 127) / 128, d.nx);
-    k_count_active<<<grid, 128, 0, st>>>(d.nx, d.nz, d.n_elem, P->m, P->dmin, P->nz_pad,
-                                         P->wtab, cnt);
+    k_count_active<<<grid, 128, 0, st>>>(g, d.nx, d.nz, d.n_elem, P->wtab, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       cudaFree(cnt);
@@ -965,7 +1050,7 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.err = scratch;
   b.timeouts = scratch + P->scratch_ints - 1;
   b.expect_extra = P->expect_extra;
-  c->sb.func = bf_func(P->K, P->apod, P->comp);
+  c->sb.func = bf_func(P->K, P->apod, P->comp, P->full);
   c->sb.grid = dim3(std::max(1, std::min(b.n_items, P->blocks_per_sm * P->num_sms)));
   c->sb.block = dim3(P->threads);
   c->sb.smem = P->smem;
@@ -1351,43 +1436,44 @@ int* plan_timeout_counter(pa_plan_s* P) {
   return P && P->scratch[0] ? P->scratch[0] + P->scratch_ints - 1 : nullptr;
 }
 
-cudaError_t bf_launch(int order, bool apod, bool comp, const BfParams& p, int grid, int block,
-                      size_t smem, cudaStream_t s) {
+cudaError_t bf_launch(int order, bool apod, bool comp, bool full, const BfParams& p, int grid,
+                      int block, size_t smem, cudaStream_t s) {
   switch (order) {
-    case 1: return bf_launch_k1(apod, comp, p, grid, block, smem, s);
-    case 2: return bf_launch_k2(apod, comp, p, grid, block, smem, s);
-    case 3: return bf_launch_k3(apod, comp, p, grid, block, smem, s);
-    case 4: return bf_launch_k4(apod, comp, p, grid, block, smem, s);
-    case 5: return bf_launch_k5(apod, comp, p, grid, block, smem, s);
-    case 6: return bf_launch_k6(apod, comp, p, grid, block, smem, s);
-    case 7: return bf_launch_k7(apod, comp, p, grid, block, smem, s);
-    case 8: return bf_launch_k8(apod, comp, p, grid, block, smem, s);
+    case 1: return bf_launch_k1(apod, comp, full, p, grid, block, smem, s);
+    case 2: return bf_launch_k2(apod, comp, full, p, grid, block, smem, s);
+    case 3: return bf_launch_k3(apod, comp, full, p, grid, block, smem, s);
+    case 4: return bf_launch_k4(apod, comp, full, p, grid, block, smem, s);
+    case 5: return bf_launch_k5(apod, comp, full, p, grid, block, smem, s);
+    case 6: return bf_launch_k6(apod, comp, full, p, grid, block, smem, s);
+    case 7: return bf_launch_k7(apod, comp, full, p, grid, block, smem, s);
+    case 8: return bf_launch_k8(apod, comp, full, p, grid, block, smem, s);
   }
   return cudaErrorInvalidValue;
 }
-const void* bf_func(int order, bool apod, bool comp) {
+const void* bf_func(int order, bool apod, bool comp, bool full) {
   switch (order) {
-    case 1: return bf_func_k1(apod, comp);
-    case 2: return bf_func_k2(apod, comp);
-    case 3: return bf_func_k3(apod, comp);
-    case 4: return bf_func_k4(apod, comp);
-    case 5: return bf_func_k5(apod, comp);
-    case 6: return bf_func_k6(apod, comp);
-    case 7: return bf_func_k7(apod, comp);
-    case 8: return bf_func_k8(apod, comp);
+    case 1: return bf_func_k1(apod, comp, full);
+    case 2: return bf_func_k2(apod, comp, full);
+    case 3: return bf_func_k3(apod, comp, full);
+    case 4: return bf_func_k4(apod, comp, full);
+    case 5: return bf_func_k5(apod, comp, full);
+    case 6: return bf_func_k6(apod, comp, full);
+    case 7: return bf_func_k7(apod, comp, full);
+    case 8: return bf_func_k8(apod, comp, full);
   }
   return nullptr;
 }
-cudaError_t bf_occupancy(int order, bool apod, bool comp, int block, size_t smem, int* n) {
+cudaError_t bf_occupancy(int order, bool apod, bool comp, bool full, int block, size_t smem,
+                         int* n) {
   switch (order) {
-    case 1: return bf_occupancy_k1(apod, comp, block, smem, n);
-    case 2: return bf_occupancy_k2(apod, comp, block, smem, n);
-    case 3: return bf_occupancy_k3(apod, comp, block, smem, n);
-    case 4: return bf_occupancy_k4(apod, comp, block, smem, n);
-    case 5: return bf_occupancy_k5(apod, comp, block, smem, n);
-    case 6: return bf_occupancy_k6(apod, comp, block, smem, n);
-    case 7: return bf_occupancy_k7(apod, comp, block, smem, n);
-    case 8: return bf_occupancy_k8(apod, comp, block, smem, n);
+    case 1: return bf_occupancy_k1(apod, comp, full, block, smem, n);
+    case 2: return bf_occupancy_k2(apod, comp, full, block, smem, n);
+    case 3: return bf_occupancy_k3(apod, comp, full, block, smem, n);
+    case 4: return bf_occupancy_k4(apod, comp, full, block, smem, n);
+    case 5: return bf_occupancy_k5(apod, comp, full, block, smem, n);
+    case 6: return bf_occupancy_k6(apod, comp, full, block, smem, n);
+    case 7: return bf_occupancy_k7(apod, comp, full, block, smem, n);
+    case 8: return bf_occupancy_k8(apod, comp, full, block, smem, n);
   }
   return cudaErrorInvalidValue;
 }
@@ -1424,6 +1510,7 @@ pa_status pa_plan_footprint(const pa_plan_desc* desc, int32_t n_frames, size_t* 
   pa_plan_s P;
   P.d = *desc;
   configure(&P);
+  if ((s = check_table_size(&P)) != PA_OK) return s;
   size_t b = table_bytes(&P);
   b += (3 + (size_t)P.d.max_batch * 3) * sizeof(int);  // scratch, as pa_plan allocates it
   const size_t elt = desc->rf_dtype == PA_RF_F32 ? 4 : 2;
@@ -1453,6 +1540,8 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->chunk_steps = P->nc;
   info->lane_rows = 1 << P->lane_rows_log2;
   info->tmem_columns = P->tmem_cols;
+  info->delay_table = P->full ? PA_TABLE_FULL : PA_TABLE_LATTICE;
+  info->table_bytes = delay_table_bytes(P);
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);
@@ -1700,6 +1789,6 @@ const char* pa_status_str(pa_status s) {
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int32_t pa_version(void) { return 103; }
+int32_t pa_version(void) { return 104; }
 
 }  // extern "C"

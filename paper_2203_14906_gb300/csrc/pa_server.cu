@@ -71,10 +71,11 @@ std::string plan_key(const pa_plan_desc& d) {
   char buf[640];
   snprintf(buf, sizeof buf,
            "%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%u|%d|%.17g|%.17g|%.17g|"
-           "%.17g|%.17g|%d|%d",
+           "%.17g|%.17g|%d|%d|%d",
            d.n_elem, d.pitch_m, d.c_m_s, d.fs_hz, d.t0_s, d.n_samples, d.nx, d.nz, d.x0_m, d.x1_m,
            d.z0_m, d.z1_m, d.order_k, d.outputs, (int)d.rf_dtype, d.f_number, d.f0_hz,
-           d.band_lo_hz, d.band_hi_hz, d.dyn_range_db, d.compensated, (int)d.interp);
+           d.band_lo_hz, d.band_hi_hz, d.dyn_range_db, d.compensated, (int)d.interp,
+           (int)d.delay_table);
   return buf;
 }
 

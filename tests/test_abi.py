@@ -64,7 +64,9 @@ def test_validation_rejects_bad_descriptors():
         dict(n_samples=1),
         dict(z0_m=-1e-3),
         dict(x1_m=-9.6e-3),  # empty lateral extent
-        dict(nx=100),  # pitch / dx not an integer
+        dict(nx=100, delay_table="lattice"),  # pitch / dx not an integer
+        dict(nx=32, delay_table="lattice"),  # pitch / dx = 1/2
+        dict(nx=64 * 64, delay_table="lattice"),  # pitch / dx = 64 > 32
     ]
     for over in bad:
         w = dict(wl)
@@ -84,8 +86,28 @@ def test_validation_rejects_bad_descriptors():
     d.interp = 2
     assert _status(d)[0] == _native.PA_EINVAL
     assert _status(_native.make_desc(dict(wl, interp="nearest")))[0] == _native.PA_OK
-    # pitch/dx = 64 exceeds the supported lattice
-    w = dict(wl, nx=64 * 64)
+    d = _native.make_desc(wl)
+    d.delay_table = 3
+    assert _status(d)[0] == _native.PA_EINVAL
+
+
+def test_grids_off_the_lattice_take_the_full_table():
+    """Any lateral pitch is accepted; off the lattice the footprint counts
+    the full table (8 bytes per pixel, padded tile column and virtual
+    channel, plus 4 with apodisation), and a table above the stated maximum
+    is refused."""
+    wl = synth.workload("cfg1")
+    base = _status(_native.make_desc(wl))[1]
+    for nx, span in ((100, 19.2e-3), (32, 19.2e-3), (64 * 64, 19.2e-3), (7, 3e-3)):
+        w = dict(wl, nx=nx, x0_m=-span / 2, x1_m=span / 2)
+        st, nbytes = _status(_native.make_desc(w))
+        assert st == _native.PA_OK, nx
+        # nv >= N + 6 virtual channels, nz_pad = 128 rows
+        assert nbytes - base >= nx * (64 + 6) * 128 * 8 - 3 * 1024 * 1024, nx
+    # lattice grids keep the small table unless the full one is asked for
+    st, nbytes_full = _status(_native.make_desc(dict(wl, delay_table="full")))
+    assert st == _native.PA_OK and nbytes_full - base > 0.9 * 128 * 71 * 128 * 8
+    w = dict(wl, nx=16384, nz=2048)  # 16384 x 71 x 2048 x 8 B > 16 GiB
     assert _status(_native.make_desc(w))[0] == _native.PA_EUNSUPPORTED
 
 
