@@ -121,7 +121,7 @@ typedef struct pa_plan_s* pa_plan_t;
 /* Read-only facts about a plan (for tests, benchmarks and admission). */
 typedef struct {
   int32_t lattice_m;          /* pitch / lateral pixel pitch (lattice table;
-                                 1 with the full table)                    */
+                                 0 with the full table)                    */
   int32_t tile_x, tile_z;     /* pixel tile of one thread block            */
   int32_t window;             /* RF samples staged per channel per tile    */
   int32_t n_tiles;            /* tiles per frame                           */

@@ -4,7 +4,7 @@
 //
 // Delay tables: LATTICE (one entry per lattice offset and depth, shared by
 // the kC pairs of a thread at one channel step, see below) or FULL (one
-// entry per pixel and element, Section 5's precomputed delays for any
+// 32-bit entry per pixel and element, Section 5's precomputed delays for any
 // grid); the FULL kernel reads kC entries per step, one per pair.
 //
 // Work decomposition (one persistent CTA loop over work items):
@@ -220,8 +220,9 @@ static_assert(kC == 4, "channel-base loads below read 2 x int4");
 // points a pair at a slot with exactly one tap inside the record, so a delay
 // whose taps leave the record reads (0, 0).  s_cb[cv] is the 32-bit shared
 // address of sample 0 of the channel's window, so the slot of sample n0 lives
-// at s_cb[cv] + 8 n0.  Work is spread over the whole block, four slots per
-// thread-iteration.
+// at s_cb[cv] + 8 n0 (lattice table); with the full table, whose entries
+// hold n0 - lo, it is the address of the window's first slot.  Work is
+// spread over the whole block, four slots per thread-iteration.
 template <int DT>
 __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int tile_id, int v0,
                                             int* s_cb, unsigned char* smem, uint32_t sbase) {
@@ -231,7 +232,7 @@ __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int ti
   const size_t frame_base = (size_t)frame * p.n_elem;
   for (int c = threadIdx.x; c < p.ncs; c += blockDim.x) {
     const int v = v0 + c;
-    const int lo = v < p.nv ? __ldg(lo_t + v) : 0;
+    const int lo = v < p.nv && !p.full ? __ldg(lo_t + v) : 0;
     s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - lo * 8;
   }
   const int total = p.ncs * W4;
@@ -340,7 +341,7 @@ __device__ __forceinline__ void convert_chunk(const BfParams& p, int* s_cb, cons
                                               unsigned char* smem, uint32_t sbase) {
   const int W = p.window, W4 = W >> 2;
   for (int c = threadIdx.x; c < p.ncs; c += blockDim.x)
-    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - s_lo[c] * 8;
+    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - (p.full ? 0 : s_lo[c] * 8);
   const int total = p.ncs * W4;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
@@ -560,14 +561,18 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     int fold = 0;
 
     // Table rows of this thread.  LATTICE: row t(u) = jt - dmin - m u at
-    // depth z.  FULL: the entry of pixel c (column jt + c) and channel
-    // u + c at depth z sits at fcol + (u - u0) nzp + c fcst.
+    // depth z.  FULL: the entry of pixel c (column jt + m c) and channel
+    // u + c sits at fbase0 + (u - u0) kC fcst + c fcst, the table being laid
+    // out per tile, step, pixel, row group, slot and row (the warp's 32
+    // entries of one step and pixel are contiguous).
     const int2* tcol = p.table + z;
     const float* wcol = APOD ? p.wtab + z : nullptr;
     const int row_u0 = jt - p.dmin;
     const int mstride = p.m * p.table_stride;
-    const size_t fcst = (size_t)(p.nv + 1) * p.table_stride;
-    const size_t fbase0 = (size_t)jt * p.nv * p.table_stride + z;
+    const size_t fcst = (size_t)32 * p.slots;
+    const size_t fbase0 = (size_t)tile_id * p.steps * kC * fcst +
+                          ((size_t)(warp / sg) * p.slots + sl) * (1 << lr_log2) +
+                          (lane & ((1 << lr_log2) - 1));
 
     int lo_next = 0;  // window start of my channel in the next chunk to issue
     if (p.use_tma && vk.x < vk.y) {
@@ -633,22 +638,24 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       if (u >= u_end) continue;
 
       if constexpr (FULL) {
-        // Entries (n0, a) [and weights] of the kC pairs of step uu.
-        auto load_step = [&](int2 (&e)[kC], float (&w)[kC], int uu) {
-          const size_t o = fbase0 + (size_t)(uu - p.u0) * p.table_stride;
+        // Packed entries [and weights] of the kC pairs of step uu.
+        auto load_step = [&](uint32_t (&e)[kC], float (&w)[kC], int uu) {
+          const size_t o = fbase0 + (size_t)(uu - p.u0) * kC * fcst;
 #ifdef PA_CHECK_BOUNDS
-          if (o + (kC - 1) * fcst >= (size_t)p.ndrows * p.table_stride) atomicOr(p.err, 1);
+          if (o + (kC - 1) * fcst >= (size_t)(tile_id + 1) * p.steps * kC * fcst) atomicOr(p.err, 1);
 #endif
 #pragma unroll
           for (int c = 0; c < kC; ++c) {
-            e[c] = __ldg(p.table + o + c * fcst);
+            e[c] = __ldg(p.ftab + o + c * fcst);
             if constexpr (APOD) w[c] = __ldg(p.wtab + o + c * fcst);
           }
         };
-        // kC steps from uu; the entries of the next step are loaded while
-        // the current one is evaluated (the last step of the chunk reloads
-        // its own entries instead of reading past the chunk).
-        auto fblock = [&](auto near_tag, int2 (&e)[kC], float (&w)[kC], int uu) {
+        // kC steps from uu.  The entries of the step after next are loaded
+        // while the current step is evaluated (two steps of latency cover);
+        // near the end of the chunk the last step's entries are reloaded
+        // instead of reading past it.
+        auto fblock = [&](auto near_tag, uint32_t (&e0)[kC], uint32_t (&e1)[kC],
+                          float (&w0)[kC], float (&w1)[kC], int uu) {
           constexpr bool NEAR = decltype(near_tag)::value;
           int cb[2 * kC];
           {
@@ -659,12 +666,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
           }
 #pragma unroll
           for (int tt = 0; tt < kC; ++tt) {
-            int2 e2[kC];
+            uint32_t e2[kC];
             float w2[kC];
-            load_step(e2, w2, min(uu + tt + 1, u_end - 1));
+            load_step(e2, w2, min(uu + tt + 2, u_end - 1));
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
-              int addr = cb[tt + c] + e[c].x;
+              const uint32_t q = e0[c];
+              int addr = cb[tt + c] + (int)((q & 0x1ffu) << 3);
 #ifdef PA_CHECK_BOUNDS
               if (addr < pairs_off || addr > smem_hi) {
                 atomicOr(p.err, 2);
@@ -675,17 +683,23 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
               if constexpr (NEAR) {
                 asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(addr));
               } else {
+                // 1 + a as an FP32 bit pattern: exponent 127 over the 23 bits of a
+                const float a = __uint_as_float(__funnelshift_r(q, 0x7fu, 9)) - 1.0f;
                 float2 r;
                 asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
-                s = fmaf(__int_as_float(e[c].y), r.y, r.x);
+                s = fmaf(a, r.y, r.x);
               }
-              if constexpr (APOD) s *= w[c];
+              if constexpr (APOD) s *= w0[c];
               pair_update<K>(acc[c], s);
             }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
-              e[c] = e2[c];
-              if constexpr (APOD) w[c] = w2[c];
+              e0[c] = e1[c];
+              e1[c] = e2[c];
+              if constexpr (APOD) {
+                w0[c] = w1[c];
+                w1[c] = w2[c];
+              }
             }
           }
           if constexpr (COMP) {
@@ -695,12 +709,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
             }
           }
         };
-        int2 e[kC];
-        float w[kC];
-        load_step(e, w, u);
+        uint32_t e0[kC], e1[kC];
+        float w0[kC], w1[kC];
+        load_step(e0, w0, u);
+        load_step(e1, w1, min(u + 1, u_end - 1));
         for (; u < u_end; u += kC) {
-          if (p.nearest) fblock(std::true_type{}, e, w, u);
-          else fblock(std::false_type{}, e, w, u);
+          if (p.nearest) fblock(std::true_type{}, e0, e1, w0, w1, u);
+          else fblock(std::false_type{}, e0, e1, w0, w1, u);
         }
         continue;
       } else {

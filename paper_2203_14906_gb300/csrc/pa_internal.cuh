@@ -76,16 +76,21 @@ struct BfParams {  // aligned as CUtensorMap requires
   int tmem_cols;          // TMEM columns a block allocates (compensated sums), else 0
   int n_elem, n_samples;
   long long frame_elems;  // N * Ns
-  const int2* table;      // [ndrows][nz_pad] {n0 * 8, float bits of a}; rows are
-                          // lattice offsets, or (column, virtual channel) pairs
-                          // of the full table
+  const int2* table;      // lattice table [ndrows][nz_pad] {n0 * 8, float bits of a},
+                          // rows = lattice offsets
+  const uint32_t* ftab;   // full table, in the kernel's read order: per tile,
+                          // channel step, pixel c, row group, slot, row; a in
+                          // bits 31..9 (2^-23 units), the slot n0 - window
+                          // start in bits 8..0
+  int full;               // 1: full table (channel bases are window starts)
+  int steps;              // channel steps u1 - u0
   const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)
   int table_stride;       // nz_pad
   const int4* items;      // [n_tiles * ngroups] {tile_id, grp, tx, tz}, deepest first
   const int2* slot_rg;    // [slots] {column residue r_m, column group g}
   int ndrows;
   int dmin;               // lattice offset of table row 0
-  int m;                  // pitch / dx
+  int m;                  // column stride of a thread's pixels (lattice: pitch / dx)
   int R;                  // column groups per residue in a tile
   int nxt, nzt;           // tiles along x and z
   int tile_x, tile_z;

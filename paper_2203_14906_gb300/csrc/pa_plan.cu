@@ -68,6 +68,7 @@ struct pa_plan_s {
   int m = 1, R = 1, slots = 1, warps = 1, ngroups = 1, threads = 32;
   int tile_x = 0, tile_z = 32, nxt = 0, nzt = 0, n_tiles = 0, nx_pad = 0, nz_pad = 0;
   int u0 = 0, u1 = 0, nv = 0, dmin = 0, ndrows = 0, window = 0;
+  size_t full_entries = 0;  // entries of the full table (n_tiles * steps * kC * 32 * slots)
   size_t smem = 0;
   int blocks_per_sm = 0;
   bool use_tma = false;
@@ -85,7 +86,8 @@ struct pa_plan_s {
   uint32_t warnings = 0;
   float dyn_range = 60.f;
   // device memory
-  int2* table = nullptr;
+  int2* table = nullptr;     // lattice table
+  uint32_t* ftab = nullptr;  // full table (packed entries, see k_table_full)
   float* wtab = nullptr;
   int* lo = nullptr;
   int2* urange = nullptr;
@@ -165,6 +167,31 @@ struct pa_plan_s {
 namespace {
 
 // ---------------------------------------------------------- plan kernels
+// Layout of the full table, in the order the fused kernel reads it: per
+// tile, channel step u' = u - u0, pixel c of a thread, row group rg of the
+// tile's 32 rows, warp slot sl and row zl within the group:
+//   ((((tile * steps + u') * kC + c) * RG + rg) * slots + sl) * LR + zl
+// with LR depth rows per lane group and RG = 32 / LR.  The 32 lanes of a
+// warp (LR rows x 32 / LR neighbouring slots) read 128 contiguous bytes.
+struct FullGeom {
+  int nxt, n_tiles, tile_x, tile_z, m, slots, steps, lr_log2, nx, nz, n_elem, u0, nv;
+};
+
+__host__ __device__ __forceinline__ size_t full_index(const FullGeom& f, int tile, int up, int c,
+                                                     int sl, int zt) {
+  const int lr = 1 << f.lr_log2;
+  const int rg = zt >> f.lr_log2, zl = zt & (lr - 1);
+  return ((((size_t)tile * f.steps + up) * kC + c) * (32 >> f.lr_log2) + rg) * f.slots * lr +
+         (size_t)sl * lr + zl;
+}
+
+// Pixel column of pixel c of warp slot sl in tile column tx.
+__host__ __device__ __forceinline__ int full_column(const FullGeom& f, int tx, int sl, int c) {
+  return tx * f.tile_x + (sl / f.m) * f.m * kC + (sl % f.m) + f.m * c;
+}
+// Widest RF window (slots) the packed full-table entry addresses.
+constexpr int kFullMaxWindow = 512;
+
 struct TableGeom {
   int ndrows, nzp, dmin, ns, nearest;
   double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
@@ -174,15 +201,13 @@ struct TableGeom {
   int n_elem, u0, nv;
 };
 
-// One table entry: the one-way time of flight in samples from a pixel at
-// lateral offset dxv from the element and depth zp, tau = fs (r / c - t0),
-// stored as the integer sample n0 = floor(tau) (pre-scaled by 8, the byte
-// stride of an interpolation pair) and the FP32 fraction a = tau - n0; and
-// the apodisation weight.
-__device__ void table_entry(const TableGeom& g, double dxv, double zp, size_t ti, int2* table,
-                            float* wtab) {
+// The one-way time of flight in samples from a pixel at lateral offset dxv
+// from the element and depth zp, tau = fs (r / c - t0), as the integer sample
+// n0 = floor(tau) and the fraction a = tau - n0 (nearest-sample delays,
+// Eq. 1: n0 = round(tau), a = 0).
+__device__ void delay_sample(const TableGeom& g, double dxv, double zp, int* n0_out,
+                             double* a_out) {
   const double tau = g.fs * (sqrt(dxv * dxv + zp * zp) / g.c - g.t0);
-  // linear: n0 = floor(tau), a = tau - n0; nearest (Eq. 1): n0 = round(tau), a = 0
   double fl = g.nearest ? floor(tau + 0.5) : floor(tau);
   double a = g.nearest ? 0.0 : tau - fl;
   const double lim = 1048576.0;
@@ -197,50 +222,124 @@ __device__ void table_entry(const TableGeom& g, double dxv, double zp, size_t ti
   // n0 = Ns-1 already give 0 and r[Ns-1], so no remapping is needed.)
   if (!g.nearest && n0 == -1) n0 = -2;
   if (!g.nearest && n0 == g.ns - 1) n0 = g.ns;
-  table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
-  if (wtab) {
-    float w = 0.f;
-    const double half = zp / (2.0 * g.fnum);
-    if (half > 0.0 && fabs(dxv) <= half) {
-      const double cw = cos(3.14159265358979323846 * dxv / (2.0 * half));
-      w = (float)(cw * cw);
-    }
-    wtab[ti] = w;
-  }
+  *n0_out = n0;
+  *a_out = a;
 }
 
-// Lattice table: every lattice offset d = j - m i and depth row.
+// Hann dynamic-aperture weight of an element at lateral offset dxv from a
+// pixel at depth zp (0 outside the aperture |dxv| <= zp / (2F)).
+__device__ float apod_weight(const TableGeom& g, double dxv, double zp) {
+  float w = 0.f;
+  const double half = zp / (2.0 * g.fnum);
+  if (half > 0.0 && fabs(dxv) <= half) {
+    const double cw = cos(3.14159265358979323846 * dxv / (2.0 * half));
+    w = (float)(cw * cw);
+  }
+  return w;
+}
+
+// Lateral offset x_j - x_i of pixel column j and virtual channel v (element
+// i = v + u0), both positions computed as the grid and the array define them.
+__device__ double full_dx(const TableGeom& g, int j, int v) {
+  const double xp = g.x0 + ((double)j + 0.5) * g.dx;
+  const double xi = ((double)(v + g.u0) - 0.5 * (double)(g.n_elem - 1)) * g.pitch;
+  return xp - xi;
+}
+
+__device__ double pixel_z(const TableGeom& g, int z) { return g.z0 + ((double)z + 0.5) * g.dz; }
+
+// Lattice table: every lattice offset d = j - m i and depth row, entry
+// {n0 * 8 (the byte stride of an interpolation slot), FP32 bits of a}.
 __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = blockIdx.y;
   if (z >= g.nzp || row >= g.ndrows) return;
   const double dxv = g.x_const + ((double)(g.dmin + row) + 0.5) * g.dx;
-  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
-  table_entry(g, dxv, zp, table_index(row, z, g.nzp), table, wtab);
+  const double zp = pixel_z(g, z);
+  int n0;
+  double a;
+  delay_sample(g, dxv, zp, &n0, &a);
+  const size_t ti = table_index(row, z, g.nzp);
+  table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
+  if (wtab) wtab[ti] = apod_weight(g, dxv, zp);
 }
 
-// Full table: every (pixel column j, virtual channel v) pair and depth row,
-// row j * nv + v; the lateral offset is x_j - x_i with both positions
-// computed from the grid and the array as they are defined.
-__global__ void k_table_full(TableGeom g, int2* table, float* wtab) {
-  const int z = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y, j = blockIdx.z;
-  if (z >= g.nzp) return;
-  const double xp = g.x0 + ((double)j + 0.5) * g.dx;
-  const double xi = ((double)(v + g.u0) - 0.5 * (double)(g.n_elem - 1)) * g.pitch;
-  const double zp = g.z0 + ((double)z + 0.5) * g.dz;
-  table_entry(g, xp - xi, zp, table_index(j * g.nv + v, z, g.nzp), table, wtab);
+// Full table: the entry of every (pixel, channel step) pair the fused kernel
+// evaluates (pixel c of slot sl pairs with channel u + c at step u), in the
+// layout of full_index, packed in 32 bits relative to the RF window its tile
+// stages for that channel (lo, from k_windows_full): bits 31..9 the fraction
+// a in 23 bits (truncated, so a < 1 stays below 1), bits 8..0 the slot
+// n0 - lo (the window is at most kFullMaxWindow slots wide).
+__global__ void k_table_full(TableGeom g, FullGeom f, const int* lo, uint32_t* table,
+                             float* wtab) {
+  const int tile = blockIdx.y;
+  const size_t per_tile = (size_t)f.steps * kC * 32 * f.slots;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= per_tile) return;
+  const int lr = 1 << f.lr_log2;
+  size_t t = e;
+  const int zl = (int)(t % lr);
+  t /= lr;
+  const int sl = (int)(t % f.slots);
+  t /= f.slots;
+  const int rg = (int)(t % (32 >> f.lr_log2));
+  t /= (32 >> f.lr_log2);
+  const int c = (int)(t % kC);
+  const int up = (int)(t / kC);
+  const int tx = tile % f.nxt, tz = tile / f.nxt;
+  const int j = full_column(f, tx, sl, c);
+  const int v = up + c;
+  const int z = tz * f.tile_z + rg * lr + zl;
+  const double dxv = full_dx(g, j, v);
+  const double zp = pixel_z(g, z);
+  int n0;
+  double a;
+  delay_sample(g, dxv, zp, &n0, &a);
+  const int off = n0 - lo[(size_t)tile * g.nv + v];
+  const uint32_t frac = (uint32_t)(a * 8388608.0);  // a * 2^23, a in [0, 1)
+  const size_t ti = (size_t)tile * per_tile + e;
+  table[ti] = (frac << 9) | (uint32_t)(off & 0x1ff);
+  if (wtab) wtab[ti] = apod_weight(g, dxv, zp);
+}
+
+// Pairs with a non-zero apodisation weight in the full table (real pixels
+// and elements only).
+__global__ void k_count_active_full(FullGeom f, const float* wtab, unsigned long long* count) {
+  const int tile = blockIdx.y;
+  const size_t per_tile = (size_t)f.steps * kC * 32 * f.slots;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cnt = 0;
+  if (e < per_tile) {
+    const int lr = 1 << f.lr_log2;
+    size_t t = e;
+    const int zl = (int)(t % lr);
+    t /= lr;
+    const int sl = (int)(t % f.slots);
+    t /= f.slots;
+    const int rg = (int)(t % (32 >> f.lr_log2));
+    t /= (32 >> f.lr_log2);
+    const int c = (int)(t % kC);
+    const int up = (int)(t / kC);
+    const int j = full_column(f, tile % f.nxt, sl, c);
+    const int z = (tile / f.nxt) * f.tile_z + rg * lr + zl;
+    const int i = up + c + f.u0;
+    if (j < f.nx && z < f.nz && i >= 0 && i < f.n_elem &&
+        wtab[(size_t)tile * per_tile + e] > 0.f)
+      cnt = 1;
+  }
+  for (int s = 16; s >= 1; s >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, s);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(count, cnt);
 }
 
 struct TileGeom {
   int nxt, nzt, tile_x, tile_z, m, dmin, nzp, nv, u0, ndrows;
-  int full;  // 1: rows are (column, virtual channel) pairs, j * nv + v
+  int full;  // 1: full table (laid out as full_index says)
 };
 
-// Table row of pixel column j and virtual channel v (lattice: offset
-// d = j - m i; full: j * nv + v).
+// Lattice-table row of pixel column j and virtual channel v (offset
+// d = j - m i, i = v + u0).
 __device__ __forceinline__ int tile_row(const TileGeom& g, int j, int v) {
-  return g.full ? j * g.nv + v : j - g.m * (v + g.u0) - g.dmin;
+  return j - g.m * (v + g.u0) - g.dmin;
 }
 
 // First staged sample (rounded down to a multiple of 4) and window width of
@@ -268,10 +367,33 @@ __global__ void k_windows(TileGeom g, int lo_align, const int2* table, int* lo, 
   atomicMax(wmax, mx - lo_al + 1);
 }
 
+// The same windows for the full table, from the delays themselves (the
+// packed table is written relative to them afterwards).
+__global__ void k_windows_full(TableGeom tg, TileGeom g, int lo_align, int* lo, int* wmax) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (v >= g.nv) return;
+  const int tx = tile % g.nxt, tz = tile / g.nxt;
+  const int zf = tz * g.tile_z, zl = zf + g.tile_z - 1;
+  int mn = 0x7fffffff, mx = -0x7fffffff;
+  for (int jj = 0; jj < g.tile_x; ++jj) {
+    const double dxv = full_dx(tg, tx * g.tile_x + jj, v);
+    int n0;
+    double a;
+    delay_sample(tg, dxv, pixel_z(tg, zf), &n0, &a);
+    mn = min(mn, n0);
+    delay_sample(tg, dxv, pixel_z(tg, zl), &n0, &a);
+    mx = max(mx, n0);
+  }
+  const int lo_al = mn & ~(lo_align - 1);
+  lo[(size_t)tile * g.nv + v] = lo_al;
+  atomicMax(wmax, mx - lo_al + 1);
+}
+
 // Channel-step range of every warp slot.  Without apodisation every step is
 // evaluated; with it, only steps whose lattice offset has a non-zero weight on
 // the warp's deepest row (the widest aperture of its rows).
-__global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wtab,
+__global__ void k_uranges(TileGeom g, FullGeom f, int slots, int u1, int kc, const float* wtab,
                           int2* urange) {
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
   const int tile = blockIdx.y;
@@ -285,12 +407,14 @@ __global__ void k_uranges(TileGeom g, int slots, int u1, int kc, const float* wt
     int ua = u1, ub = g.u0;
     for (int u = g.u0; u < u1; ++u) {
       // lattice: the kC pixels of the slot share one entry at step u; full:
-      // pixel c (column jt + c) pairs with channel u + c
+      // pixel c (column jt + m c) pairs with channel u + c, each its own entry
       bool on = false;
-      for (int c = 0; c < (g.full ? kc : 1); ++c) {
-        const int row = tile_row(g, jt + c, u - g.u0 + c);
-        if (row < 0 || row >= g.ndrows) continue;
-        on |= wtab[table_index(row, zl, g.nzp)] > 0.f;
+      if (g.full) {
+        for (int c = 0; c < kc; ++c)
+          on |= wtab[full_index(f, tile, u - g.u0, c, sl, g.tile_z - 1)] > 0.f;
+      } else {
+        const int row = tile_row(g, jt, u - g.u0);
+        if (row >= 0 && row < g.ndrows) on = wtab[table_index(row, zl, g.nzp)] > 0.f;
       }
       if (on) {
         ua = min(ua, u);
@@ -430,21 +554,22 @@ void configure(pa_plan_s* P) {
   const double dx = (d.x1_m - d.x0_m) / d.nx;
   const int lm = lattice_m(d);
   P->full = d.delay_table == PA_TABLE_FULL || (d.delay_table == PA_TABLE_AUTO && lm == 0);
-  // the full table pairs pixel c of a thread (column jt + c) with channel
-  // u + c; no entry is shared, so the columns of a thread are neighbours
-  P->m = P->full ? 1 : lm;
   // 32-column tiles halve the staged samples per pair; small images keep
   // 16-column tiles so that there are enough tiles to fill the GPU.
   const bool big = (int64_t)d.nx * d.nz >= 512 * 512;
-  P->R = std::max(1, (big ? 8 : 4) / P->m);
   if (P->full) {
-    // the RF window of a tile spans the delays over its lateral extent:
-    // keep tiles within ~3.2 mm laterally, in a power of two of column
-    // groups (whole warps of 8-row lane groups)
-    const int rmax = (int)std::floor(3.2e-3 / (kC * dx) + 1e-9);
-    int r = 1;
-    while (2 * r <= std::min(P->R, rmax)) r *= 2;
-    P->R = r;
+    // No table entry is shared, so the column stride m of a thread's pixels
+    // is free: 4 (as the lattice has at cfg2) keeps a warp's slots on
+    // neighbouring columns, whose delays for one channel differ least, so
+    // its shared-memory gathers stay narrow.  The RF window of a tile spans
+    // the delays over its lateral extent: tiles stay within ~3.2 mm.
+    int cols = big ? 32 : 16;
+    while (cols > 8 && cols * dx > 3.2e-3) cols /= 2;
+    P->m = cols >= 16 ? 4 : 2;
+    P->R = cols / (P->m * kC);
+  } else {
+    P->m = lm;
+    P->R = std::max(1, (big ? 8 : 4) / P->m);
   }
   P->slots = P->m * P->R;
   int B = 1;
@@ -489,9 +614,10 @@ void configure(pa_plan_s* P) {
   P->u1 = P->u0 + steps;
   const int i_max = P->u1 - 1 + kC - 1;
   P->nv = i_max - P->u0 + 1;
-  if (P->full) {  // rows: (pixel column, virtual channel) pairs
+  if (P->full) {  // one entry per evaluated (pixel, channel step) pair
     P->dmin = 0;
-    P->ndrows = P->nx_pad * P->nv;
+    P->ndrows = 0;
+    P->full_entries = (size_t)P->n_tiles * steps * kC * 32 * P->slots;
   } else {
     P->dmin = -P->m * i_max;
     const int dmax = P->nx_pad - 1 + P->m * (kC - 1);
@@ -578,22 +704,21 @@ cudaError_t fused_blocks_per_sm(const pa_plan_s* P, size_t smem, int* n) {
 
 // Bytes of the delay table and its apodisation weights.
 size_t delay_table_bytes(const pa_plan_s* P) {
+  if (P->full) return P->full_entries * (sizeof(uint32_t) + (P->apod ? sizeof(float) : 0));
   return (size_t)P->ndrows * P->nz_pad * (sizeof(int2) + (P->apod ? sizeof(float) : 0));
 }
 
 pa_status check_table_size(const pa_plan_s* P) {
   if (P->full && delay_table_bytes(P) > PA_FULL_TABLE_MAX_BYTES)
     return fail(PA_EUNSUPPORTED,
-                "the full delay table of %d x %d x %d entries (%zu bytes) exceeds "
+                "the full delay table of %zu entries (%zu bytes) exceeds "
                 "PA_FULL_TABLE_MAX_BYTES",
-                P->nx_pad, P->nv, P->nz_pad, delay_table_bytes(P));
+                P->full_entries, delay_table_bytes(P));
   return PA_OK;
 }
 
 size_t table_bytes(const pa_plan_s* P) {
-  const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
-  size_t b = tab_n * sizeof(int2);
-  if (P->apod) b += tab_n * sizeof(float);
+  size_t b = delay_table_bytes(P);
   b += (size_t)P->n_tiles * P->ngroups * sizeof(int4) + (size_t)P->slots * sizeof(int2);
   b += (size_t)P->n_tiles * P->nv * sizeof(int);
   b += (size_t)P->n_tiles * P->slots * sizeof(int2);
@@ -636,6 +761,7 @@ void free_plan(pa_plan_s* P) {
   for (int s = 0; s < kHostSets; ++s)
     if (P->hs[s]) cudaStreamSynchronize(P->hs[s]);
   cudaFree(P->table);
+  cudaFree(P->ftab);
   cudaFree(P->wtab);
   cudaFree(P->lo);
   cudaFree(P->urange);
@@ -680,8 +806,12 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   pa_status s;
   const size_t tab_n = (size_t)P->ndrows * P->nz_pad;
   if ((s = check_table_size(P)) != PA_OK) return s;
-  if ((s = dalloc(P, &P->table, tab_n)) != PA_OK) return s;
-  if (P->apod && (s = dalloc(P, &P->wtab, tab_n)) != PA_OK) return s;
+  if (P->full) {
+    if ((s = dalloc(P, &P->ftab, P->full_entries)) != PA_OK) return s;
+  } else if ((s = dalloc(P, &P->table, tab_n)) != PA_OK) {
+    return s;
+  }
+  if (P->apod && (s = dalloc(P, &P->wtab, P->full ? P->full_entries : tab_n)) != PA_OK) return s;
   if ((s = dalloc(P, &P->items, (size_t)P->n_tiles * P->ngroups)) != PA_OK) return s;
   if ((s = dalloc(P, &P->slot_rg, (size_t)P->slots)) != PA_OK) return s;
   if ((s = dalloc(P, &P->lo, (size_t)P->n_tiles * P->nv)) != PA_OK) return s;
@@ -719,14 +849,6 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   tg.n_elem = d.n_elem;
   tg.u0 = P->u0;
   tg.nv = P->nv;
-  if (P->full) {
-    dim3 grid((P->nz_pad + 127) / 128, P->nv, P->nx_pad);
-    k_table_full<<<grid, 128, 0, st>>>(tg, P->table, P->wtab);
-  } else {
-    dim3 grid((P->nz_pad + 127) / 128, P->ndrows);
-    k_table<<<grid, 128, 0, st>>>(tg, P->table, P->wtab);
-  }
-  PA_CUDA(cudaGetLastError());
 
   // per-tile windows and warp ranges
   TileGeom g;
@@ -741,23 +863,43 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   g.u0 = P->u0;
   g.ndrows = P->ndrows;
   g.full = P->full ? 1 : 0;
+  FullGeom fg{P->nxt, P->n_tiles, P->tile_x, P->tile_z, P->m, P->slots, P->u1 - P->u0,
+              P->lane_rows_log2, d.nx, d.nz, d.n_elem, P->u0, P->nv};
   int* wmax = P->scratch[0] + 2;  // borrowed before first use as image maxima
-  {
-    dim3 grid((P->nv + 127) / 128, P->n_tiles);
-    k_windows<<<grid, 128, 0, st>>>(g, P->lo_align, P->table, P->lo, wmax, P->scratch[0]);
+  if (P->full) {
+    // windows first: the packed entries are written relative to them
+    dim3 gw((P->nv + 127) / 128, P->n_tiles);
+    k_windows_full<<<gw, 128, 0, st>>>(tg, g, P->lo_align, P->lo, wmax);
+    PA_CUDA(cudaGetLastError());
+    const size_t per_tile = P->full_entries / P->n_tiles;
+    dim3 gt((unsigned)((per_tile + 255) / 256), P->n_tiles);
+    k_table_full<<<gt, 256, 0, st>>>(tg, fg, P->lo, P->ftab, P->wtab);
+    PA_CUDA(cudaGetLastError());
+  } else {
+    dim3 gt((P->nz_pad + 127) / 128, P->ndrows);
+    k_table<<<gt, 128, 0, st>>>(tg, P->table, P->wtab);
+    PA_CUDA(cudaGetLastError());
+    dim3 gw((P->nv + 127) / 128, P->n_tiles);
+    k_windows<<<gw, 128, 0, st>>>(g, P->lo_align, P->table, P->lo, wmax, P->scratch[0]);
     PA_CUDA(cudaGetLastError());
   }
   {
     dim3 grid((P->slots + 31) / 32, P->n_tiles);
-    k_uranges<<<grid, 32, 0, st>>>(g, P->slots, P->u1, kC, P->wtab, P->urange);
+    k_uranges<<<grid, 32, 0, st>>>(g, fg, P->slots, P->u1, kC, P->wtab, P->urange);
     PA_CUDA(cudaGetLastError());
   }
   unsigned long long* cnt = nullptr;
   if (P->apod) {
     PA_CUDA(cudaMalloc(&cnt, sizeof(unsigned long long)));
     PA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-    dim3 grid((d.nz + 127) / 128, d.nx);
-    k_count_active<<<grid, 128, 0, st>>>(g, d.nx, d.nz, d.n_elem, P->wtab, cnt);
+    if (P->full) {
+      const size_t per_tile = P->full_entries / P->n_tiles;
+      dim3 grid((unsigned)((per_tile + 255) / 256), P->n_tiles);
+      k_count_active_full<<<grid, 256, 0, st>>>(fg, P->wtab, cnt);
+    } else {
+      dim3 grid((d.nz + 127) / 128, d.nx);
+      k_count_active<<<grid, 128, 0, st>>>(g, d.nx, d.nz, d.n_elem, P->wtab, cnt);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       cudaFree(cnt);
@@ -778,6 +920,11 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   if (head[0] != 0) return fail(PA_ECUDA, "plan build: table row outside range (flag %d)", head[0]);
   const int width = head[2];
   P->window = ((std::max(width, 1) + 3) / 4) * 4;
+  if (P->full && P->window > kFullMaxWindow)
+    return fail(PA_EUNSUPPORTED,
+                "RF window of %d samples per channel exceeds the %d the full delay table "
+                "addresses; use a finer depth grid",
+                P->window, kFullMaxWindow);
   PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
 
   // TMA box geometry of one staged channel
@@ -1015,6 +1162,9 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.n_samples = d.n_samples;
   b.frame_elems = (long long)d.n_elem * d.n_samples;
   b.table = P->table;
+  b.ftab = P->ftab;
+  b.full = P->full ? 1 : 0;
+  b.steps = P->u1 - P->u0;
   b.wtab = P->wtab;
   b.table_stride = P->nz_pad;
   b.items = P->items;
@@ -1522,7 +1672,7 @@ pa_status pa_plan_footprint(const pa_plan_desc* desc, int32_t n_frames, size_t* 
 
 pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   if (!P || !info) return fail(PA_EINVAL, "null argument");
-  info->lattice_m = P->m;
+  info->lattice_m = P->full ? 0 : P->m;
   info->tile_x = P->tile_x;
   info->tile_z = P->tile_z;
   info->window = P->window;

@@ -93,9 +93,9 @@ def test_validation_rejects_bad_descriptors():
 
 def test_grids_off_the_lattice_take_the_full_table():
     """Any lateral pitch is accepted; off the lattice the footprint counts
-    the full table (8 bytes per pixel, padded tile column and virtual
-    channel, plus 4 with apodisation), and a table above the stated maximum
-    is refused."""
+    the full table (4 bytes per padded pixel and channel step, N + 3 or more
+    steps, plus 4 with apodisation), and a table above the stated maximum is
+    refused."""
     wl = synth.workload("cfg1")
     base = _status(_native.make_desc(wl))[1]
     for nx, span in ((100, 19.2e-3), (32, 19.2e-3), (64 * 64, 19.2e-3), (7, 3e-3)):
@@ -103,11 +103,11 @@ def test_grids_off_the_lattice_take_the_full_table():
         st, nbytes = _status(_native.make_desc(w))
         assert st == _native.PA_OK, nx
         # nv >= N + 6 virtual channels, nz_pad = 128 rows
-        assert nbytes - base >= nx * (64 + 6) * 128 * 8 - 3 * 1024 * 1024, nx
+        assert nbytes - base >= nx * 64 * 128 * 4 - 3 * 1024 * 1024, nx
     # lattice grids keep the small table unless the full one is asked for
     st, nbytes_full = _status(_native.make_desc(dict(wl, delay_table="full")))
-    assert st == _native.PA_OK and nbytes_full - base > 0.9 * 128 * 71 * 128 * 8
-    w = dict(wl, nx=16384, nz=2048)  # 16384 x 71 x 2048 x 8 B > 16 GiB
+    assert st == _native.PA_OK and nbytes_full - base > 0.9 * 128 * 64 * 128 * 4
+    w = dict(wl, nx=32768, nz=2048)  # 32768 x 2048 x 68 steps x 4 B > 16 GiB
     assert _status(_native.make_desc(w))[0] == _native.PA_EUNSUPPORTED
 
 

@@ -556,7 +556,7 @@ def test_random_off_lattice_geometries(case):
     out, info, deq = run_gpu(wl, rf, k, rf_dtype=dtype, compensated=int(dtype != "f32"),
                              max_batch=int(rng.integers(1, 3)))
     assert info["device_error_flags"] == 0
-    assert info["delay_table"] == 2 and info["lattice_m"] == 1
+    assert info["delay_table"] == 2 and info["lattice_m"] == 0
     what = (f"case {case}: N={wl['n_elem']} pitch/dx={0.3e-3 * wl['nx'] / (wl['x1_m'] - wl['x0_m']):.4f} "
             f"grid={wl['nx']}x{wl['nz']} Ns={wl['n_samples']} k={k} {dtype} "
             f"F#={wl['f_number']} {wl['interp']}")
@@ -576,11 +576,13 @@ def test_off_lattice_full_size_cfg2_400_columns(k):
 
 @pytest.mark.parametrize("kind", ["fp32", "bf16_apod"])
 def test_full_table_equals_lattice_table(kind):
-    """On a lattice grid both table forms hold the same FP64 delays, so the
-    images agree to the rounding of the FP32 sums: plain sums add the same
-    values in the same channel order (1e-6 of the peak); compensated sums
+    """On a lattice grid both table forms hold the same FP64 delays: the
+    lattice entry keeps the fraction a rounded to FP32, the full entry
+    truncated to 23 bits (within 1.2e-7 of each other), and compensated sums
     fold their FP32 partial sums at channels that depend on a column's place
-    within its thread, which differs between the forms (1e-5)."""
+    within its thread, which differs between the forms.  The images agree to
+    1e-5 of their peaks, far inside the 1e-4 gate each meets against the
+    oracle."""
     if kind == "fp32":
         wl, k, dt, comp = synth.workload("cfg1"), 3, "f32", 0
     else:
@@ -594,7 +596,7 @@ def test_full_table_equals_lattice_table(kind):
         outs[form] = out
     a, b = outs["lattice"], outs["full"]
     peak = np.max(np.abs(a), axis=(-2, -1), keepdims=True)
-    assert np.max(np.abs(a - b) / np.maximum(peak, 1e-30)) <= (1e-6 if comp == 0 else 1e-5)
+    assert np.max(np.abs(a - b) / np.maximum(peak, 1e-30)) <= 1e-5
     assert_parity(compare(b, oracle_frames(wl, deq, k)), TOL32, what=f"full table {kind}")
 
 
