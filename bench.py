@@ -422,17 +422,20 @@ def precision_report(pa, wl, k, frames64, rf_dtype, comp, tol):
     return rep
 
 
-def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
+def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush, order=None,
+              steps=None):
     """Device-timed steps of one arithmetic form; returns (times_s, profile, plan_info)."""
     import synth
 
+    order = args.order if order is None else order
+    steps = args.steps if steps is None else steps
     F = frames64.shape[0]
     store, _ = synth.quantize(frames64, rf_dtype)
     if rf_dtype == "bf16":
         rf = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
     else:
         rf = torch.from_numpy(store).cuda()
-    desc = pa.make_desc(wl, order_k=args.order, outputs=7, rf_dtype=rf_dtype, max_batch=F,
+    desc = pa.make_desc(wl, order_k=order, outputs=7, rf_dtype=rf_dtype, max_batch=F,
                         compensated=comp)
     plan = pa.Plan(desc, stream=stream)
     stages = pa.PA_STAGE_LOG
@@ -445,8 +448,8 @@ def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
         plan.profile_read()
         plan.profile(True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for s in range(args.steps):
+               for _ in range(steps)]
+        for s in range(steps):
             flush()
             evs[s][0].record(stream)
             pa.beamform(plan, rf, stages, out=out, stream=stream)
@@ -458,6 +461,75 @@ def time_form(pa, torch, wl, args, rf_dtype, comp, frames64, stream, flush):
     info = plan.info()
     plan.close()
     return times, prof, info
+
+
+def fused_roofline(prof, info, frames, k, peak):
+    """Fused-kernel time per launch and its fraction of the FP32-issue
+    roofline (active pairs x ops per pair / time / peak)."""
+    ms, n = prof["bf_fused"]
+    t = ms / 1e3 / max(n, 1)
+    achieved = info["active_pairs"] * frames * ops_per_pair(k) / t / 1e12
+    return {"kernel_ms_per_launch": t * 1e3, "achieved_top_s": achieved, "frac": achieved / peak,
+            "ops_per_pair": ops_per_pair(k)}
+
+
+def off_lattice_bench(pa, torch, args, stream, flush, peak, lattice_value):
+    """The headline workload on a grid off the lattice: cfg2 geometry (128 el
+    x 2048 samples, 38.4 x 40 mm) on 400 x 512 pixels, pitch / dx = 3.125,
+    so the plan takes the full per-pixel delay table; FP32 RF, k as the
+    headline, 32 frames per step."""
+    import synth
+
+    wl = synth.workload("cfg2", nx=400)
+    F = args.frames
+    frames = np.stack([synth.make_frame(wl, 11, f) for f in range(F)])
+    steps = max(3, min(args.steps, 50))
+    t, prof, info = time_form(pa, torch, wl, args, "f32", 0, frames, stream, flush, steps=steps)
+    value = wl["nx"] * wl["nz"] * wl["n_elem"] * F * steps / sum(t) / 1e9
+    out = {
+        "workload": (f"cfg2 geometry on a {wl['nx']}x{wl['nz']} grid (pitch / dx = 3.125, off the "
+                     f"lattice): full per-pixel delay table, FP32 RF, k={args.order}, {F} frames"),
+        "value": value, "unit": UNIT, "vs_lattice_headline": value / lattice_value,
+        "delay_table": "full" if info["delay_table"] == 2 else "lattice",
+        "table_bytes": info["table_bytes"], "steps": steps,
+        "roofline": fused_roofline(prof, info, F, args.order, peak),
+    }
+    return out
+
+
+def cfg3_bench(pa, torch, args, stream, flush, peak):
+    """cfg3, the reduced-precision workload: 256 el x 4096 samples at 50 MHz,
+    1024 x 1024 grid over 76.8 x 60 mm, 8 frames per step.  Rates of the
+    BF16 + Kahan form and the plain FP32 form at k = 3 and k = 5 (device
+    time, L2 flushed between steps), and the errors of every image of two
+    frames against the FP64 oracle for BF16 and FP16 storage."""
+    import synth
+
+    wl = synth.workload("cfg3")
+    F = 8
+    frames = np.stack([synth.make_frame(wl, wl["seeds"][0], f) for f in range(F)])
+    steps = max(3, min(args.steps, 20))
+    pairs = wl["nx"] * wl["nz"] * wl["n_elem"] * F
+    out = {"workload": ("cfg3: 256 el x 4096 samples @ 50 MHz, 1024x1024 grid, 20 points over "
+                        "40 dB, unit-RMS RF; DAS+DMAS+DMAS-k, log images, 8 frames per step"),
+           "frames_per_step": F, "steps": steps, "unit": UNIT}
+    for k in (3, 5):
+        leg = {}
+        for name, dt, comp in (("bf16_kahan", "bf16", 1), ("fp32", "f32", 0)):
+            t, prof, info = time_form(pa, torch, wl, args, dt, comp, frames, stream, flush,
+                                      order=k, steps=steps)
+            leg[name] = {"value": pairs * steps / sum(t) / 1e9,
+                         "roofline": fused_roofline(prof, info, F, k, peak)}
+        leg["bf16_kahan_vs_fp32"] = leg["bf16_kahan"]["value"] / leg["fp32"]["value"]
+        out[f"k{k}"] = leg
+    rep_frames = frames[:2]
+    out["precision_report"] = {
+        "bf16_kahan_k3": precision_report(pa, wl, 3, rep_frames, "bf16", 1, 5e-3),
+        "f16_kahan_k3": precision_report(pa, wl, 3, rep_frames, "f16", 1, 5e-3),
+        "bf16_kahan_k5": precision_report(pa, wl, 5, rep_frames, "bf16", 1, 5e-3),
+        "against": "FP64 oracle, every image of 2 frames (worst frame per output)",
+    }
+    return out
 
 
 def metrics_rois(wl):
@@ -748,6 +820,8 @@ def run_ours(args):
             "vs_fp32_form": v_nn * ws / value,
             "kernel_ms_per_launch": prof_nn["bf_fused"][0] / max(prof_nn["bf_fused"][1], 1),
         }
+        extras["off_lattice_form"] = off_lattice_bench(pa, torch, args, stream, flush, peak,
+                                                       value / ws)
         if rank == 0:
             nrep = min(8, frames64.shape[0])
             extras["precision_report"] = {
@@ -757,6 +831,7 @@ def run_ours(args):
                             "per output)"),
             }
             extras["metrics_form"] = metrics_bench(pa, torch, wl, args, frames64, stream, flush)
+            extras["precision_cfg3"] = cfg3_bench(pa, torch, args, stream, flush, peak)
             extras["oracle_timing"] = oracle_timing()
             extras["throughput_batch"] = throughput_batch(pa, torch, args, stream, flush)
             done, v_cpu, dt, cores = oracle_run(wl, frames64, k, args.cpu_seconds)

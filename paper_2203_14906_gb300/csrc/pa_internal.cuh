@@ -20,12 +20,15 @@ constexpr int kC = 4;
 constexpr int kNCMax = 72;
 constexpr int kNCSMax = kNCMax + kC - 1;
 // Channel steps between Kahan folds of the compensated power sums: plain
-// FP32 partial sums over 32 channels, compensated across folds.  Measured on
-// GB300 (BF16 RF, 128 channels, k = 3): folding every 8 / 16 / 32 steps takes
-// 0.937 / 0.894 / 0.877 ms per 32-frame launch, and the error against the
-// FP64 oracle on the same (dequantised) RF stays below 5e-7 of the image
-// peak for k = 3..5 at 256 channels.
-constexpr int kFoldBlocks = 8;  // blocks of kC steps
+// FP32 partial sums over 64 channels, compensated across folds.  Every fold
+// loads and stores each accumulator's totals in TMEM (about 100 instructions
+// per thread), so its issue cost per pair halves with the interval.
+// Measured on GB300 (BF16 RF, 128 channels, k = 3, 32 frames, fused kernel
+// per launch): folding every 8 / 16 / 32 steps took 0.937 / 0.894 / 0.877 ms
+// in an earlier build with the totals in registers; with the totals in TMEM
+// every 32 / 64 steps takes 0.676 / 0.661 ms (cfg3, 256 channels: k = 3
+// 1.289 / 1.259 ms, k = 5 1.586 / 1.547 ms).
+constexpr int kFoldBlocks = 16;  // blocks of kC steps
 constexpr int kMaxOrder = 8;
 // Shared-memory layout of the fused kernel: work-item words, the TMA
 // mbarrier (8 B at 16) and the TMEM base address (4 B at 24), channel bases
