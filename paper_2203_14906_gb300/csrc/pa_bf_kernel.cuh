@@ -436,15 +436,19 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
 // Kahan fold of the partial sums into the running totals held in TMEM.  The
 // warp executes it converged: the plans that use it give every lane of a warp
 // the same channel-step range (one slot per warp, or slots without
-// apodisation, whose ranges are all the full aperture).
-template <int NA>
-__device__ __forceinline__ void kahan_fold_tmem(float (&acc)[kC][NA], uint32_t tmem) {
+// apodisation, whose ranges are all the full aperture).  LAZY: the first
+// fold of a work item folds into zero totals without loading them, so
+// nothing has to zero TMEM before the item (apodised plans, whose items
+// mostly end before their first fold); otherwise the totals are zeroed when
+// the item starts and every fold loads them (no branch in the fold).
+template <int NA, bool LAZY>
+__device__ __forceinline__ void kahan_fold_tmem(float (&acc)[kC][NA], uint32_t tmem, bool first) {
   static_assert(kC == 4, "totals and compensation terms of one accumulator fill 8 columns");
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
-    float t[8];
-    tmem_ld8(tmem + 8 * q, t);
+    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (!LAZY || !first) tmem_ld8(tmem + 8 * q, t);
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
       const float y = acc[c][q] - t[4 + c];
@@ -454,6 +458,25 @@ __device__ __forceinline__ void kahan_fold_tmem(float (&acc)[kC][NA], uint32_t t
       acc[c][q] = 0.f;
     }
     tmem_st8(tmem + 8 * q, t);
+  }
+}
+
+// The last fold of a work item, straight into the values the epilogue
+// combines: totals plus the remaining partial sums, compensated, rounded
+// once to FP32 (total minus compensation), nothing stored back.
+template <int NA>
+__device__ __forceinline__ void kahan_final_tmem(float (&acc)[kC][NA], uint32_t tmem) {
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    float t[8];
+    tmem_ld8(tmem + 8 * q, t);
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      const float y = acc[c][q] - t[4 + c];
+      const float s = t[c] + y;
+      acc[c][q] = s - ((s - t[c]) - y);
+    }
   }
 }
 
@@ -553,12 +576,18 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     for (int c = 0; c < kC; ++c)
 #pragma unroll
       for (int q = 0; q < NA; ++q) acc[c][q] = 0.f;
-    if constexpr (TSUM) {
+    // Lazy TMEM totals for apodised plans: an item's narrow aperture rarely
+    // reaches a fold.  Measured on GB300 (fused kernel per launch): the
+    // throughput batch 2.711 -> 2.664 ms lazy; without apodisation the
+    // branch cost more than it saved (cfg2 BF16 k = 3 0.661 -> 0.680 ms).
+    constexpr bool LAZY = APOD;
+    if constexpr (TSUM && !LAZY) {
       const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < NA; ++q) tmem_st8(tmem + 8 * q, z8);
     }
     int fold = 0;
+    bool tsum_live = !LAZY;  // this item's totals are in TMEM
 
     // Table rows of this thread.  LATTICE: row t(u) = jt - dmin - m u at
     // depth z.  FULL: the entry of pixel c (column jt + m c) and channel
@@ -704,7 +733,8 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
           }
           if constexpr (COMP) {
             if (++fold == kFoldBlocks) {
-              kahan_fold_tmem<NA>(acc, tmem);
+              kahan_fold_tmem<NA, LAZY>(acc, tmem, !tsum_live);
+              tsum_live = true;
               fold = 0;
             }
           }
@@ -773,7 +803,8 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         }
         if constexpr (COMP) {
           if (++fold == kFoldBlocks) {
-            kahan_fold_tmem<NA>(acc, tmem);
+            kahan_fold_tmem<NA, LAZY>(acc, tmem, !tsum_live);
+            tsum_live = true;
             fold = 0;
           }
         }
@@ -796,7 +827,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       }  // LATTICE
     }
     if (timed_out) break;
-    if constexpr (TSUM) kahan_fold_tmem<NA>(acc, tmem);
+    // compensated sums: the TMEM totals combine with the last partial sums;
+    // a lazy item that never folded (at most kFoldBlocks blocks of steps)
+    // already holds its sums
+    if constexpr (TSUM) {
+      if (tsum_live) kahan_final_tmem<NA>(acc, tmem);
+    }
     if (threadIdx.x == 0 && (!p.use_tma || vk.x >= vk.y)) {
       s_item[0] = s_item[2];
       s_item[1] = 0;
@@ -805,21 +841,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     // ---- epilogue (FP64 e_k) and store -----------------------------------
     const size_t plane = (size_t)p.nx * p.nz;
     const size_t fbase = (size_t)frame * p.planes * plane;
-    if constexpr (TSUM) {  // compensated totals minus compensations, read by the whole warp
-#pragma unroll
-      for (int q = 0; q < NA; ++q) {
-        float t[8];
-        tmem_ld8(tmem + 8 * q, t);
-#pragma unroll
-        for (int c = 0; c < kC; ++c) acc[c][q] = t[c] - t[4 + c];
-      }
-    }
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
       const int j = jt + p.m * c;
       if (j < p.nx && z < p.nz) {
-        // plain sums, or compensated totals minus compensations (read from
-        // TMEM above), rounded once to FP32
+        // plain sums, or compensated totals minus compensations rounded once
+        // to FP32 (kahan_final_tmem)
         float V[NA];
 #pragma unroll
         for (int q = 0; q < NA; ++q) V[q] = acc[c][q];
