@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip precision form and cpu baseline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-requests", type=int, default=6000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--form", default="fp32", choices=["fp32", "precision"],
                     help="arithmetic form of the headline leg: FP32 RF and plain sums, or BF16 "
@@ -640,65 +640,177 @@ def throughput_batch(pa, torch, args, stream, flush):
     }
 
 
-def serving_bench(pa, args, rf_dtype, comp):
-    """Replay the cfg4 Poisson trace through the continuous-batching server."""
-    import torch
+class _ServeSet:
+    """Requests of cfg4 traces for one arithmetic form: pinned RF frames per
+    (channels, samples) class, one descriptor per plan class, a ring of
+    pinned output buffers (results are not read; timing only)."""
 
-    import synth
-    from paper_2203_14906_gb300.serving import Server, percentiles
+    RING = 64
 
-    trace = synth.serving_mix(args.serve_requests, seed=31, rate_hz=args.serve_rate)
-    pool = {}
-    for _, wl in trace:
-        key = (wl["n_elem"], wl["n_samples"])
-        if key not in pool:
-            fr = []
-            for i in range(2):
-                store, _ = synth.quantize(synth.make_frame(wl, 31, 1000 + i), rf_dtype)
-                t = torch.from_numpy(store.view(np.int16) if rf_dtype == "bf16" else store)
-                fr.append(t.pin_memory())
-            pool[key] = fr
-    ring_n = 64
-    ring = torch.empty((ring_n, 3 * 1024 * 1024), dtype=torch.float32).pin_memory()
-    descs = {}
-    reqs = []
-    for i, (t_arr, wl) in enumerate(trace):
-        dk = (wl["n_elem"], wl["n_samples"], wl["nx"], wl["order_k"])
-        if dk not in descs:
-            descs[dk] = pa.make_desc(wl, order_k=wl["order_k"], outputs=7, rf_dtype=rf_dtype,
-                                     compensated=comp)
-        rf = pool[(wl["n_elem"], wl["n_samples"])][i % 2]
-        reqs.append((t_arr, descs[dk], rf, wl["nx"] * wl["nz"] * wl["n_elem"]))
-    with Server(budget_bytes=16 << 30, slots=4, max_batch=8, stages=pa.PA_STAGE_LOG) as srv:
-        # warm-up: make every plan resident before the timed replay
-        warm = []
-        seen = set()
-        for j, (_, d, rf, _) in enumerate(reqs):
-            if id(d) in seen:
-                continue
-            seen.add(id(d))
-            warm.append(srv.submit(d, rf.data_ptr(), ring[len(warm) % ring_n].data_ptr()))
-        for t in warm:
-            srv.wait(t)
+    def __init__(self, pa, rf_dtype, comp):
+        import torch
+
+        import synth
+
+        self.pa, self.rf_dtype, self.comp = pa, rf_dtype, comp
+        self.pool, self.descs = {}, {}
+        self.ring = torch.empty((self.RING, 3 * 1024 * 1024), dtype=torch.float32).pin_memory()
+        self._synth = synth
+
+    def requests(self, n, seed, rate_hz):
+        """[(arrival_s, desc, rf, pairs)] of a seeded Poisson trace."""
+        import torch
+
+        synth = self._synth
+        out = []
+        for i, (t_arr, wl) in enumerate(synth.serving_mix(n, seed=seed, rate_hz=rate_hz)):
+            key = (wl["n_elem"], wl["n_samples"])
+            if key not in self.pool:
+                fr = []
+                for j in range(2):
+                    store, _ = synth.quantize(synth.make_frame(wl, 31, 1000 + j), self.rf_dtype)
+                    t = torch.from_numpy(store.view(np.int16) if self.rf_dtype == "bf16" else store)
+                    fr.append(t.pin_memory())
+                self.pool[key] = fr
+            dk = (wl["n_elem"], wl["n_samples"], wl["nx"], wl["order_k"])
+            if dk not in self.descs:
+                self.descs[dk] = self.pa.make_desc(wl, order_k=wl["order_k"], outputs=7,
+                                                   rf_dtype=self.rf_dtype, compensated=self.comp)
+            out.append((t_arr, self.descs[dk], self.pool[key][i % 2],
+                        wl["nx"] * wl["nz"] * wl["n_elem"]))
+        return out
+
+    def warm(self, srv):
+        """One request per plan class, so every plan is resident."""
+        for i, d in enumerate(self.descs.values()):
+            rf = self.pool[(d.n_elem, d.n_samples)][0]
+            srv.wait(srv.submit(d, rf.data_ptr(), self.ring[i % self.RING].data_ptr()))
+
+    def replay(self, srv, reqs, timed_arrivals=True, local=0):
+        """Submit a trace (arrival times replayed, or every request at once)
+        and wait for all of it; served rate, latency percentiles, clocks."""
+        from paper_2203_14906_gb300.serving import percentiles
+
+        clk = ClockSampler(local)
+        clk.start()
         st0 = srv.stats()
-        # every request is queued before the first arrival (the submit loop
-        # cannot lag the trace), then the server replays the arrival times
-        t0 = srv.now() + 0.5
-        tickets = [srv.submit(d, rf.data_ptr(), ring[i % ring_n].data_ptr(), t0 + t_arr)
+        t0 = srv.now() + 0.2
+        tickets = [srv.submit(d, rf.data_ptr(), self.ring[i % self.RING].data_ptr(),
+                              t0 + (t_arr if timed_arrivals else 0.0))
                    for i, (t_arr, d, rf, _) in enumerate(reqs)]
         res = [srv.wait(t) for t in tickets]
         st1 = srv.stats()
-    lat = [r["latency_ms"] for r in res if r["status"] == 0]
-    span = max(r["done_s"] for r in res) - t0
-    pairs = sum(p for *_, p in reqs)
-    out = {"frames": len(res), "failed": sum(r["status"] != 0 for r in res),
-           "offered_frames_per_s": args.serve_rate,
-           "served_frames_per_s": len(res) / span, "gpixel_ch_per_s": pairs / span / 1e9,
-           "latency_ms_mean": float(np.mean(lat)) if lat else None,
-           "batches": st1["batches"] - st0["batches"],
-           "mean_batch_frames": float(np.mean([r["batch_frames"] for r in res])),
-           "plans_resident": st1["plans_resident"], "device_bytes_peak": st1["bytes_peak"]}
-    out.update({f"latency_ms_{k}": v for k, v in percentiles(lat).items()})
+        clocks = clk.stop()
+        lat = [r["latency_ms"] for r in res if r["status"] == 0]
+        span = max(r["done_s"] for r in res) - (t0 if timed_arrivals else
+                                                 min(r["start_s"] for r in res))
+        # the requests above the 99th percentile: queue wait (arrival to
+        # issue) against service (issue to completion seen), and their classes
+        tail = {}
+        if lat:
+            cut = float(np.percentile(lat, 99))
+            slow = [(r, rq) for r, rq in zip(res, reqs) if r["status"] == 0 and r["latency_ms"] >= cut]
+            cls = {}
+            for r, (_, d, _, _) in slow:
+                k = f"N{d.n_elem} Ns{d.n_samples} {d.nx}^2 k{d.order_k}"
+                cls[k] = cls.get(k, 0) + 1
+            tail = {"wait_ms_median": float(np.median([(r["start_s"] - r["arrival_s"]) * 1e3
+                                                       for r, _ in slow])),
+                    "service_ms_median": float(np.median([(r["done_s"] - r["start_s"]) * 1e3
+                                                          for r, _ in slow])),
+                    "arrival_s_span": [float(min(r["arrival_s"] for r, _ in slow) - t0),
+                                       float(max(r["arrival_s"] for r, _ in slow) - t0)],
+                    "classes": sorted(cls.items(), key=lambda kv: -kv[1])[:3]}
+        out = {"frames": len(res), "failed": sum(r["status"] != 0 for r in res),
+               "served_frames_per_s": len(res) / span,
+               "gpixel_ch_per_s": sum(p for *_, p in reqs) / span / 1e9,
+               "mean_batch_frames": float(np.mean([r["batch_frames"] for r in res])),
+               "batches": st1["batches"] - st0["batches"],
+               "plans_resident": st1["plans_resident"], "device_bytes_peak": st1["bytes_peak"],
+               "latency_ms_mean": float(np.mean(lat)) if lat else None,
+               "sm_mhz_median": clocks["sm_mhz"] if clocks else None,
+               "clock_reasons": clocks["reasons"] if clocks else None,
+               "p99_tail": tail}
+        out.update({f"latency_ms_{q}": v for q, v in percentiles(lat).items()})
+        return out
+
+
+def _spread(runs, key):
+    v = [r[key] for r in runs if r.get(key) is not None]
+    if not v:
+        return None
+    m = float(np.median(v))
+    return {"median": m, "min": float(min(v)), "max": float(max(v)),
+            "spread_of_median": (max(v) - min(v)) / m if m else None}
+
+
+SERVER_CFG = dict(budget_bytes=16 << 30, slots=4, max_batch=8)
+
+
+def serving_legs(pa, args, local):
+    """cfg4 serving, per arithmetic form (BF16 + Kahan and plain FP32):
+    * offered: the stated trace (Poisson, --serve-rate frames/s, plans
+      resident), three repeats with their own seeds;
+    * saturation: every request queued at once (closed queue), three repeats:
+      the maximum sustained frames/s and Gpixel.ch/s;
+    * load points: Poisson traces at 30 / 60 / 90 % of the measured
+      saturation rate, three repeats each: p50 / p99 latency;
+    * cold: the stated trace on a fresh server with no plan resident (plans
+      are built on the server's builder thread as their first request comes).
+    Every run records the median SM clock sampled while it ran."""
+    from paper_2203_14906_gb300.serving import Server
+
+    n_sat = 4000
+    out = {"workload": (f"cfg4 mix: N in {{64,128,256}}, Ns in {{1024,2048,4096}} @ 40 MHz, grid "
+                        "{256,512,1024}^2, k uniform in 2..5; DAS+DMAS+DMAS-k log images "
+                        "returned to pinned host memory; server: 4 slots, batches up to 8 "
+                        "frames of one descriptor, 16 GiB budget"),
+           "offered_frames_per_s": args.serve_rate}
+    for form, (dt, comp) in (("bf16_kahan", ("bf16", 1)), ("fp32", ("f32", 0))):
+        ss = _ServeSet(pa, dt, comp)
+        offered_reqs = [ss.requests(args.serve_requests, 31 + r, args.serve_rate) for r in range(3)]
+        sat_reqs = [ss.requests(n_sat, 131 + r, 1e6) for r in range(3)]
+        leg = {}
+        with Server(**SERVER_CFG, stages=pa.PA_STAGE_LOG) as srv:
+            ss.warm(srv)
+            offered = [ss.replay(srv, rq, True, local) for rq in offered_reqs]
+            sat = [ss.replay(srv, rq, False, local) for rq in sat_reqs]
+            cap = float(np.median([r["served_frames_per_s"] for r in sat]))
+            loads = {}
+            for frac in (0.3, 0.6, 0.9):
+                rate = frac * cap
+                n = int(min(20000, max(1000, rate * 1.5)))
+                traces = [ss.requests(n, 231 + r, rate) for r in range(3)]
+                ss.warm(srv)  # any plan class these traces add is resident too
+                runs = [ss.replay(srv, rq, True, local) for rq in traces]
+                loads[f"{int(frac * 100)}pct"] = {
+                    "offered_frames_per_s": rate, "frames_per_run": n,
+                    "p99_tail": [r["p99_tail"] for r in runs],
+                    "served_frames_per_s": _spread(runs, "served_frames_per_s"),
+                    "latency_ms_p50": _spread(runs, "latency_ms_p50"),
+                    "latency_ms_p99": _spread(runs, "latency_ms_p99"),
+                    "mean_batch_frames": _spread(runs, "mean_batch_frames"),
+                    "sm_mhz_median": [r["sm_mhz_median"] for r in runs]}
+        leg["offered"] = {
+            "runs": offered,
+            "latency_ms_p50": _spread(offered, "latency_ms_p50"),
+            "latency_ms_p99": _spread(offered, "latency_ms_p99"),
+            "served_frames_per_s": _spread(offered, "served_frames_per_s")}
+        leg["saturation"] = {
+            "frames_per_run": n_sat, "runs": sat,
+            "served_frames_per_s": _spread(sat, "served_frames_per_s"),
+            "gpixel_ch_per_s": _spread(sat, "gpixel_ch_per_s"),
+            "mean_batch_frames": _spread(sat, "mean_batch_frames")}
+        leg["load_points"] = loads
+        with Server(**SERVER_CFG, stages=pa.PA_STAGE_LOG) as srv:
+            leg["cold"] = ss.replay(srv, offered_reqs[0], True, local)
+        out[form] = leg
+    b, f = out["bf16_kahan"]["saturation"], out["fp32"]["saturation"]
+    ratio = b["gpixel_ch_per_s"]["median"] / f["gpixel_ch_per_s"]["median"]
+    noise = max(b["gpixel_ch_per_s"]["spread_of_median"], f["gpixel_ch_per_s"]["spread_of_median"])
+    out["saturation_bf16_kahan_vs_fp32"] = {
+        "ratio": ratio, "run_to_run_spread": noise,
+        "difference_exceeds_spread": abs(ratio - 1.0) > noise}
     return out
 
 
@@ -793,14 +905,7 @@ def run_ours(args):
     # serving first: the CPU-heavy oracle legs below would compete with the
     # server's scheduler thread for host cores
     if not args.no_serving and rank == 0:
-        extras["serving"] = {
-            "workload": (f"cfg4 mix: {args.serve_requests} requests, Poisson {args.serve_rate:g} "
-                         "frames/s; N in {64,128,256}, Ns in {1024,2048,4096} @ 40 MHz, grid "
-                         "{256,512,1024}^2, k uniform in 2..5; DAS+DMAS+DMAS-k log images "
-                         "returned to pinned host memory"),
-            "bf16_kahan": serving_bench(pa, args, "bf16", 1),
-            "fp32": serving_bench(pa, args, "f32", 0),
-        }
+        extras["serving"] = serving_legs(pa, args, local)
 
     if not args.no_extras:
         # reduced-precision form on the same workload: BF16 RF + Kahan sums

@@ -154,6 +154,13 @@ typedef struct {
                                  blocks per SM x tmem_columns <= 512       */
   int32_t delay_table;        /* PA_TABLE_LATTICE or PA_TABLE_FULL         */
   size_t table_bytes;         /* bytes of the delay (+ apodisation) table  */
+  int32_t tmem_dense;         /* 1: a fused-kernel block holds more TMEM
+                                 columns than its share of the SM's 512 by
+                                 registers (blocks of <= 3 warps), so blocks
+                                 of another compensated kernel on the same
+                                 SM could wait for columns; the server never
+                                 overlaps such a plan with another
+                                 compensated batch                         */
 } pa_plan_info;
 
 /*

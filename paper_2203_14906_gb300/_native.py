@@ -117,6 +117,7 @@ class PlanInfo(ctypes.Structure):
         ("tmem_columns", ctypes.c_int32),
         ("delay_table", ctypes.c_int32),
         ("table_bytes", ctypes.c_size_t),
+        ("tmem_dense", ctypes.c_int32),
     ]
 
     def as_dict(self):

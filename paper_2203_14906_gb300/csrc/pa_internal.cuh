@@ -194,6 +194,11 @@ void set_error_message(const char* msg);
 // Device address of the plan's running count of timed-out waits (the word
 // pa_beamform's launches update), for the server's completion check.
 int* plan_timeout_counter(pa_plan_s* P);
+// Device memory the plan owns (without synchronising, unlike pa_plan_get_info).
+size_t plan_device_bytes(const pa_plan_s* P);
+// TMEM columns per fused-kernel block and whether the plan is TMEM-dense
+// (its blocks can hold more TMEM than their register share of an SM).
+void plan_tmem(const pa_plan_s* P, int* cols, bool* dense);
 
 cudaError_t post_configure(size_t smem);
 cudaError_t post_launch(const PostParams& p, cudaStream_t s);

@@ -1586,6 +1586,33 @@ int* plan_timeout_counter(pa_plan_s* P) {
   return P && P->scratch[0] ? P->scratch[0] + P->scratch_ints - 1 : nullptr;
 }
 
+size_t plan_device_bytes(const pa_plan_s* P) { return P ? P->device_bytes : 0; }
+
+// A compensated plan's fused-kernel blocks hold tmem_cols TMEM columns each.
+// Whatever blocks share an SM, their registers add up to at most the SM's
+// register file, so if every block's columns are within its register share
+// of the SM's 512 columns (cols * regs_sm <= 512 * regs_block), blocks of
+// any mix of such kernels never ask for more TMEM than the SM has.  A plan
+// outside that bound (blocks of 3 or fewer warps) is TMEM-dense: its blocks
+// can fill an SM's TMEM while registers remain, so a block of another
+// compensated kernel landing there would wait in tcgen05.alloc.
+void plan_tmem(const pa_plan_s* P, int* cols, bool* dense) {
+  *cols = P ? P->tmem_cols : 0;
+  *dense = false;
+  if (!P || !P->tmem_cols) return;
+  cudaFuncAttributes a;
+  int regs_sm = 65536;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, P->device);
+  if (cudaFuncGetAttributes(&a, bf_func(P->K, P->apod, P->comp, P->full)) != cudaSuccess) {
+    cudaGetLastError();
+    *dense = true;  // unknown: treat as dense (serialised with other compensated batches)
+    return;
+  }
+  const size_t warps = (size_t)(P->threads + 31) / 32;
+  const size_t regs_block = (size_t)((a.numRegs * 32 + 255) / 256) * 256 * warps;
+  *dense = (size_t)P->tmem_cols * (size_t)regs_sm > (size_t)kTmemColsPerSm * regs_block;
+}
+
 cudaError_t bf_launch(int order, bool apod, bool comp, bool full, const BfParams& p, int grid,
                       int block, size_t smem, cudaStream_t s) {
   switch (order) {
@@ -1692,6 +1719,12 @@ pa_status pa_plan_get_info(pa_plan_t P, pa_plan_info* info) {
   info->tmem_columns = P->tmem_cols;
   info->delay_table = P->full ? PA_TABLE_FULL : PA_TABLE_LATTICE;
   info->table_bytes = delay_table_bytes(P);
+  {
+    int cols = 0;
+    bool dense = false;
+    plan_tmem(P, &cols, &dense);
+    info->tmem_dense = dense ? 1 : 0;
+  }
   info->device_error_flags = 0;
   {
     DeviceGuard g(P->device);

@@ -1,10 +1,14 @@
 // pa_server.cu -- continuous-batching request server over the plan ABI.
 //
-// One scheduler thread owns every CUDA call of the server: plan creation,
-// device buffers (a stream-ordered memory pool), the H2D copy, pa_beamform
-// and the D2H copy of each batch, and completion polling.  Callers only
-// enqueue requests and wait for results, so the plan objects (which are not
-// thread-safe) are touched by one thread.
+// One scheduler thread issues every batch: device buffers (a stream-ordered
+// memory pool), the H2D copy, pa_beamform and the D2H copy, and completion
+// polling.  A builder thread creates new plans on a stream of its own, so a
+// request with a new descriptor does not hold up batches whose plans are
+// resident: the scheduler reserves the plan's memory, queues the build and
+// goes on with other requests; a finished build is handed back to the
+// scheduler, which alone inserts plans into (and destroys them from) its
+// cache.  Callers only enqueue requests and wait for results, so each plan
+// object (not thread-safe) is touched by one thread at a time.
 //
 // Scheduling: requests become visible at their arrival time.  Whenever a
 // slot (stream) is free, the oldest visible request whose plan is not busy
@@ -13,6 +17,12 @@
 // plan's tables) fit in the device budget next to the batches in flight.
 // Completion is detected by polling each slot's event; the request's latency
 // is the server-clock time of that detection minus its arrival time.
+//
+// Tensor memory: compensated plans keep their Kahan totals in TMEM (512
+// columns per SM).  Blocks whose columns stay within their register share of
+// an SM can share it with any other such blocks; a TMEM-dense plan (see
+// pa::plan_tmem) is never in flight together with another compensated batch,
+// so no block waits in tcgen05.alloc for another kernel's columns.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -37,6 +47,7 @@ struct Request {
   uint64_t ticket = 0;
   pa_plan_desc desc{};
   std::string key;
+  size_t key_hash = 0;  // hash of key, compared first
   const void* rf = nullptr;
   float* out = nullptr;
   size_t rf_bytes = 0, out_bytes = 0;
@@ -53,8 +64,22 @@ struct PlanEntry {
   pa_plan_t plan = nullptr;
   size_t bytes = 0;
   bool busy = false;
+  bool building = false;  // queued for, or in, the builder thread
+  int tmem_cols = 0;      // > 0: compensated plan (Kahan totals in TMEM)
+  bool tmem_dense = false;
   uint64_t last_used = 0;
   int timeouts_seen = 0;  // timed-out waits of this plan already charged to a batch
+};
+
+// A plan the builder thread finished (or failed to build).
+struct Built {
+  std::string key;
+  pa_plan_t plan = nullptr;
+  pa_status status = PA_OK;
+  std::string error;
+  size_t bytes = 0;
+  int tmem_cols = 0;
+  bool tmem_dense = false;
 };
 
 struct Slot {
@@ -102,6 +127,14 @@ struct pa_server_s {
   cudaMemPool_t pool = nullptr;
   cudaStream_t plan_stream = nullptr;
   uint64_t use_clock = 0;
+  int comp_in_flight = 0, dense_in_flight = 0;  // compensated / TMEM-dense batches in flight
+  int plans_count = 0;  // plans.size(), kept under mu for pa_server_get_stats
+  // builder thread (queue and results guarded by mu)
+  std::deque<std::pair<std::string, pa_plan_desc>> build_q;
+  std::vector<Built> built;
+  std::condition_variable cv_build;
+  bool stop_build = false;
+  std::thread builder;
   // statistics (guarded by mu)
   uint64_t submitted = 0, completed = 0, failed = 0, batches = 0;
   size_t in_use = 0, peak = 0;
@@ -139,6 +172,10 @@ struct pa_server_s {
         in_use -= s.bytes;
       }
       if (e != cudaSuccess) cudaGetLastError();
+      if (s.pe->tmem_cols > 0) {
+        --comp_in_flight;
+        if (s.pe->tmem_dense) --dense_in_flight;
+      }
       s.pe->busy = false;
       s.busy = false;
       s.reqs.clear();
@@ -164,64 +201,75 @@ struct pa_server_s {
       if (cur + need <= cfg.device_budget_bytes && !over_count) return;
       auto victim = plans.end();
       for (auto it = plans.begin(); it != plans.end(); ++it) {
-        if (it->second.busy) continue;
+        if (it->second.busy || it->second.building) continue;
         if (victim == plans.end() || it->second.last_used < victim->second.last_used) victim = it;
       }
       if (victim == plans.end()) return;
       pa_destroy(victim->second.plan);
+      const size_t freed = victim->second.bytes;
+      plans.erase(victim);
       {
         std::lock_guard<std::mutex> lk(mu);
-        in_use -= victim->second.bytes;
+        in_use -= freed;
+        plans_count = (int)plans.size();
       }
-      plans.erase(victim);
     }
   }
 
   // Try to issue one batch on slot s; returns true if something was issued
   // or failed (the visible list changed).
   bool issue(Slot& s) {
+    // a TMEM-dense request waiting for the compensated batches in flight to
+    // drain holds back later compensated requests, so it is not starved
+    bool hold_comp = false;
     for (auto it = visible.begin(); it != visible.end(); ++it) {
       Request* head = *it;
       auto pit = plans.find(head->key);
-      if (pit != plans.end() && pit->second.busy) continue;  // plan in flight elsewhere
-      std::vector<std::list<Request*>::iterator> pick{it};
-      for (auto jt = std::next(it); jt != visible.end() && (int)pick.size() < cfg.max_batch; ++jt)
-        if ((*jt)->key == head->key) pick.push_back(jt);
-      const int nf = (int)pick.size();
-      const size_t buf_rf = align_up(head->rf_bytes * nf), buf_out = align_up(head->out_bytes * nf);
-      size_t plan_bytes = 0;
       if (pit == plans.end()) {
+        // new descriptor: reserve the plan's memory and queue its build;
+        // requests of resident plans go on meanwhile
         pa_plan_desc d = head->desc;
         d.max_batch = cfg.max_batch;
+        size_t plan_bytes = 0;
         if (pa_plan_footprint(&d, 0, &plan_bytes) != PA_OK) plan_bytes = 0;
+        evict_for(plan_bytes, true);
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          if (in_use + plan_bytes > cfg.device_budget_bytes) continue;  // wait for memory
+          in_use += plan_bytes;
+          peak = std::max(peak, in_use);
+          build_q.emplace_back(head->key, d);
+        }
+        PlanEntry pe;
+        pe.building = true;
+        pe.bytes = plan_bytes;
+        plans.emplace(head->key, pe);
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          plans_count = (int)plans.size();
+        }
+        cv_build.notify_one();
+        continue;
       }
-      const size_t need = buf_rf + buf_out + plan_bytes;
-      evict_for(need, pit == plans.end());
+      if (pit->second.building || pit->second.busy) continue;  // being built / in flight
+      if (pit->second.tmem_cols > 0) {
+        // TMEM: a dense plan never shares the GPU with another compensated batch
+        if (hold_comp) continue;
+        if (pit->second.tmem_dense ? comp_in_flight > 0 : dense_in_flight > 0) {
+          if (pit->second.tmem_dense) hold_comp = true;
+          continue;
+        }
+      }
+      std::vector<std::list<Request*>::iterator> pick{it};
+      for (auto jt = std::next(it); jt != visible.end() && (int)pick.size() < cfg.max_batch; ++jt)
+        if ((*jt)->key_hash == head->key_hash && (*jt)->key == head->key) pick.push_back(jt);
+      const int nf = (int)pick.size();
+      const size_t buf_rf = align_up(head->rf_bytes * nf), buf_out = align_up(head->out_bytes * nf);
+      const size_t need = buf_rf + buf_out;
+      evict_for(need, false);
       {
         std::lock_guard<std::mutex> lk(mu);
         if (in_use + need > cfg.device_budget_bytes) return false;  // wait for memory
-      }
-      if (pit == plans.end()) {
-        pa_plan_desc d = head->desc;
-        d.max_batch = cfg.max_batch;
-        PlanEntry pe;
-        const pa_status st = pa_plan(&d, plan_stream, &pe.plan);
-        if (st != PA_OK) {
-          std::lock_guard<std::mutex> lk(mu);
-          finish(head, st, now());
-          visible.erase(it);
-          cv_done.notify_all();
-          return true;
-        }
-        pa_plan_info inf;
-        pa_plan_get_info(pe.plan, &inf);
-        pe.bytes = inf.device_bytes;
-        {
-          std::lock_guard<std::mutex> lk(mu);
-          in_use += pe.bytes;
-          peak = std::max(peak, in_use);
-        }
-        pit = plans.emplace(head->key, pe).first;
       }
       PlanEntry& pe = pit->second;
       void* rf_dev = nullptr;
@@ -264,6 +312,10 @@ struct pa_server_s {
       }
       s.busy = true;
       s.pe = &pe;
+      if (pe.tmem_cols > 0) {
+        ++comp_in_flight;
+        if (pe.tmem_dense) ++dense_in_flight;
+      }
       s.bytes = buf_rf + buf_out;
       in_use += s.bytes;
       peak = std::max(peak, in_use);
@@ -281,6 +333,82 @@ struct pa_server_s {
     return false;
   }
 
+  // Plans the builder finished: resident from now on (or, if the build
+  // failed, every waiting request with that descriptor completes with the
+  // build's status).
+  bool adopt_built() {
+    std::vector<Built> done;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      done.swap(built);
+    }
+    if (done.empty()) return false;
+    for (Built& b : done) {
+      auto pit = plans.find(b.key);
+      if (pit == plans.end()) {  // cannot happen: entries being built are never evicted
+        if (b.plan) pa_destroy(b.plan);
+        continue;
+      }
+      PlanEntry& pe = pit->second;
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= pe.bytes;  // the reservation, replaced by what the plan holds
+      if (b.status != PA_OK) {
+        const double t = now();
+        for (auto it = visible.begin(); it != visible.end();) {
+          if ((*it)->key == b.key) {
+            finish(*it, b.status, t);
+            it = visible.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        plans.erase(pit);
+        plans_count = (int)plans.size();
+        cv_done.notify_all();
+        continue;
+      }
+      pe.plan = b.plan;
+      pe.bytes = b.bytes;
+      pe.building = false;
+      pe.tmem_cols = b.tmem_cols;
+      pe.tmem_dense = b.tmem_dense;
+      in_use += pe.bytes;
+      peak = std::max(peak, in_use);
+    }
+    return true;
+  }
+
+  void build_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+      std::pair<std::string, pa_plan_desc> job;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_build.wait(lk, [&] { return stop_build || !build_q.empty(); });
+        if (stop_build) return;
+        job = build_q.front();
+        build_q.pop_front();
+      }
+      Built b;
+      b.key = job.first;
+      b.status = pa_plan(&job.second, plan_stream, &b.plan);
+      // Batches are launched kernel by kernel: with batch sizes 1..max_batch
+      // per plan, graph launch would instantiate a new graph on the
+      // scheduler thread for every new (plan, batch size), each a stall of
+      // all slots' issue.
+      if (b.status == PA_OK) b.status = pa_plan_use_graph(b.plan, 0);
+      if (b.status == PA_OK) {
+        b.bytes = pa::plan_device_bytes(b.plan);
+        pa::plan_tmem(b.plan, &b.tmem_cols, &b.tmem_dense);
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        built.push_back(std::move(b));
+      }
+      cv_sched.notify_one();
+    }
+  }
+
   void loop() {
     cudaSetDevice(device);
     for (;;) {
@@ -296,7 +424,7 @@ struct pa_server_s {
         bool busy = false;
         for (auto& s : slots) busy = busy || s.busy;
         if (stop && !busy) break;
-        if (!busy && visible.empty()) {
+        if (!busy && visible.empty() && built.empty()) {
           // Nothing to run or poll.  Sleep until shortly before the next
           // arrival (or a submit); the last stretch is spun, since a timed
           // wake-up of the thread comes tens of microseconds late.
@@ -311,7 +439,8 @@ struct pa_server_s {
           continue;
         }
       }
-      bool progress = reap();
+      bool progress = adopt_built();
+      progress = reap() || progress;
       if (!stop) {
         for (auto& s : slots) {
           if (s.busy || visible.empty()) continue;
@@ -391,6 +520,7 @@ pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
     return PA_ECUDA;
   }
   S->t0 = clock_type::now();
+  S->builder = std::thread([S] { S->build_loop(); });
   S->th = std::thread([S] { S->loop(); });
   *out = S;
   return PA_OK;
@@ -412,6 +542,7 @@ pa_status pa_server_submit(pa_server_t S, const pa_plan_desc* desc, const void* 
   Request* r = new Request();
   r->desc = d;
   r->key = plan_key(d);
+  r->key_hash = std::hash<std::string>{}(r->key);
   r->rf = rf_host;
   r->out = out_host;
   r->rf_bytes = (size_t)d.n_elem * d.n_samples * (d.rf_dtype == PA_RF_F32 ? 4 : 2);
@@ -484,7 +615,7 @@ pa_status pa_server_get_stats(pa_server_t S, pa_server_stats* st) {
   st->batches = S->batches;
   st->bytes_in_use = S->in_use;
   st->bytes_peak = S->peak;
-  st->plans_resident = (int32_t)S->plans.size();
+  st->plans_resident = S->plans_count;
   return PA_OK;
 }
 
@@ -498,6 +629,15 @@ pa_status pa_server_destroy(pa_server_t S) {
   if (S->th.joinable()) S->th.join();
   {
     std::lock_guard<std::mutex> lk(S->mu);
+    S->stop_build = true;
+  }
+  S->cv_build.notify_all();
+  if (S->builder.joinable()) S->builder.join();
+  for (auto& b : S->built)
+    if (b.plan) pa_destroy(b.plan);
+  S->built.clear();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
     const double t = S->now();
     for (auto& p : S->pending) S->finish(p.second, PA_EBUSY, t);
     for (Request* r : S->visible) S->finish(r, PA_EBUSY, t);
@@ -507,7 +647,8 @@ pa_status pa_server_destroy(pa_server_t S) {
     S->by_ticket.clear();
   }
   S->cv_done.notify_all();
-  for (auto& kv : S->plans) pa_destroy(kv.second.plan);
+  for (auto& kv : S->plans)
+    if (kv.second.plan) pa_destroy(kv.second.plan);
   for (auto& s : S->slots) {
     cudaStreamSynchronize(s.st);
     cudaStreamDestroy(s.st);

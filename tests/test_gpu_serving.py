@@ -198,3 +198,74 @@ def test_served_trace_requests_match_oracle():
             g, rr = o.numpy()[0, oi], ref[name]
             sel = rr >= -6.0
             assert np.max(np.abs(g[sel] - rr[sel])) <= 0.05, (wl["n_elem"], wl["nx"], name)
+
+
+def test_plan_builds_do_not_hold_up_resident_plans():
+    """A request with a new descriptor is built on the builder thread: a
+    request of a resident plan submitted right after it runs while the new
+    plan is still being built (a large apodised full-table plan)."""
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300.serving import Server
+
+    small, ks = _mix_workloads()[0]
+    # apodised, off the lattice (pitch / dx = 7.68): a 983 x 1024 full
+    # table, whose FP64 build takes much longer than a small frame's batch
+    big = synth.workload("cfg5", nx=983, rf_dtype="bf16", compensated=1)
+    kb = 4
+    fs, fb = _frame(small, 7), _frame(big, 8)
+    with Server(budget_bytes=8 << 30, slots=4, max_batch=1) as srv:
+        o = _out(pa, small, ks)
+        assert srv.wait(srv.submit(pa.make_desc(small, order_k=ks), fs.data_ptr(),
+                                   o.data_ptr()))["status"] == 0  # small plan resident
+        ob, os_ = _out(pa, big, kb), _out(pa, small, ks)
+        tb = srv.submit(pa.make_desc(big, order_k=kb), fb.data_ptr(), ob.data_ptr())
+        ts = srv.submit(pa.make_desc(small, order_k=ks), fs.data_ptr(), os_.data_ptr())
+        rb, rs = srv.wait(tb, timeout_ms=120000), srv.wait(ts, timeout_ms=120000)
+    assert rb["status"] == 0 and rs["status"] == 0
+    # the resident plan's request completed before the new plan's batch began
+    assert rs["done_s"] < rb["start_s"], (rs, rb)
+    assert float(ob.abs().sum()) > 0
+
+
+def test_tmem_dense_plan_never_overlaps_compensated_batches():
+    """A compensated plan whose blocks are small (2 warps: a coarse lateral
+    grid, full table) could hold more TMEM per SM than its register share;
+    the server keeps its batches apart from every other compensated batch
+    while other batches still overlap each other."""
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300.serving import Server
+
+    dense_wl = synth.workload("cfg1", nx=48, rf_dtype="bf16", compensated=1)  # dx = 0.4 mm
+    with pa.Plan(pa.make_desc(dense_wl, order_k=3)) as plan:
+        info = plan.info()
+    assert info["tmem_columns"] > 0 and info["threads"] <= 96 and info["tmem_dense"] == 1
+    others = _mix_workloads()
+    for w, k in others:
+        with pa.Plan(pa.make_desc(w, order_k=k)) as plan:
+            assert plan.info()["tmem_dense"] == 0
+    keep, reqs = [], []
+    with Server(budget_bytes=4 << 30, slots=4, max_batch=1) as srv:
+        # make every plan resident first, so the burst below is pure scheduling
+        for i, (w, k) in enumerate(others + [(dense_wl, 3)]):
+            f, o = _frame(w, 40 + i), _out(pa, w, k)
+            keep.append((f, o))
+            assert srv.wait(srv.submit(pa.make_desc(w, order_k=k), f.data_ptr(),
+                                       o.data_ptr()))["status"] == 0
+        t0 = srv.now() + 0.2
+        for rep in range(4):
+            for i, (w, k) in enumerate(others + [(dense_wl, 3)]):
+                f, o = _frame(w, 60 + 5 * rep + i), _out(pa, w, k)
+                keep.append((f, o))
+                t = srv.submit(pa.make_desc(w, order_k=k), f.data_ptr(), o.data_ptr(),
+                               arrival_s=t0 + 1e-4 * rep)
+                reqs.append((w is dense_wl, t))
+        res = [(dense, srv.wait(t, timeout_ms=60000)) for dense, t in reqs]
+    assert all(r["status"] == 0 for _, r in res)
+    dense_iv = [(r["start_s"], r["done_s"]) for d, r in res if d]
+    other_iv = [(r["start_s"], r["done_s"]) for d, r in res if not d]
+    for a0, a1 in dense_iv:
+        for b0, b1 in other_iv:
+            assert a1 <= b0 or b1 <= a0, ((a0, a1), (b0, b1))
+    # the other (non-dense) compensated batches still overlapped one another
+    iv = sorted(other_iv)
+    assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1))
