@@ -159,7 +159,8 @@ class ClockSampler:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+         "clocks.mem,temperature.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -189,7 +190,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
+        sm, mx, reasons, mem, temp = [], 0.0, set(), [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -203,10 +204,20 @@ class ClockSampler:
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+            try:
+                mem.append(float(f[9]))
+                temp.append(float(f[10]))
+            except (IndexError, ValueError):
+                pass
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if mem:
+            out["mem_mhz_median"] = statistics.median(mem)
+        if temp:
+            out["temp_c_max"] = max(temp)
+        return out
 
 
 # ------------------------------------------------------------------ helpers
@@ -718,6 +729,7 @@ class _ServeSet:
                                                        for r, _ in slow])),
                     "service_ms_median": float(np.median([(r["done_s"] - r["start_s"]) * 1e3
                                                           for r, _ in slow])),
+                    "device_ms_median": float(np.median([r["device_ms"] for r, _ in slow])),
                     "arrival_s_span": [float(min(r["arrival_s"] for r, _ in slow) - t0),
                                        float(max(r["arrival_s"] for r, _ in slow) - t0)],
                     "classes": sorted(cls.items(), key=lambda kv: -kv[1])[:3]}
@@ -728,8 +740,11 @@ class _ServeSet:
                "batches": st1["batches"] - st0["batches"],
                "plans_resident": st1["plans_resident"], "device_bytes_peak": st1["bytes_peak"],
                "latency_ms_mean": float(np.mean(lat)) if lat else None,
+               "device_ms_mean": float(np.mean([r["device_ms"] for r in res])),
                "sm_mhz_median": clocks["sm_mhz"] if clocks else None,
                "clock_reasons": clocks["reasons"] if clocks else None,
+               "mem_mhz_median": clocks.get("mem_mhz_median") if clocks else None,
+               "temp_c_max": clocks.get("temp_c_max") if clocks else None,
                "p99_tail": tail}
         out.update({f"latency_ms_{q}": v for q, v in percentiles(lat).items()})
         return out

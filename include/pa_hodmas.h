@@ -359,6 +359,9 @@ typedef struct {
   double done_s;              /* the scheduler saw its batch complete          */
   double latency_ms;          /* done_s - arrival_s                            */
   int32_t batch_frames;       /* frames in its batch                           */
+  float device_ms;            /* device time of its batch's stream work, from
+                                 before the RF upload to after the download
+                                 (CUDA events); 0 if the batch failed          */
 } pa_request_result;
 
 typedef struct {

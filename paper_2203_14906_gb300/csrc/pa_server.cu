@@ -54,6 +54,7 @@ struct Request {
   double arrival = 0, start = 0, done = 0;
   pa_status status = PA_OK;
   int batch = 0;
+  float device_ms = 0.f;  // its batch's device time
   bool finished = false;
 };
 
@@ -85,6 +86,8 @@ struct Built {
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t ev_start = nullptr;  // timing pair around the batch's stream work
+  cudaEvent_t ev_end = nullptr;
   int* h_timeouts = nullptr;  // pinned copy of the plan's timed-out-wait count after the batch
   bool busy = false;
   std::vector<Request*> reqs;
@@ -166,9 +169,17 @@ struct pa_server_s {
         s.pe->timeouts_seen = *s.h_timeouts;
         done = PA_ETIMEOUT;  // the fused kernel gave up waiting for its staging copies
       }
+      float dev_ms = 0.f;
+      if (done == PA_OK && cudaEventElapsedTime(&dev_ms, s.ev_start, s.ev_end) != cudaSuccess) {
+        cudaGetLastError();
+        dev_ms = 0.f;
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
-        for (Request* r : s.reqs) finish(r, done, t);
+        for (Request* r : s.reqs) {
+          r->device_ms = dev_ms;
+          finish(r, done, t);
+        }
         in_use -= s.bytes;
       }
       if (e != cudaSuccess) cudaGetLastError();
@@ -274,7 +285,8 @@ struct pa_server_s {
       PlanEntry& pe = pit->second;
       void* rf_dev = nullptr;
       void* out_dev = nullptr;
-      cudaError_t e = cudaMallocFromPoolAsync(&rf_dev, buf_rf, pool, s.st);
+      cudaError_t e = cudaEventRecord(s.ev_start, s.st);
+      if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&rf_dev, buf_rf, pool, s.st);
       if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&out_dev, buf_out, pool, s.st);
       pa_status st = PA_OK;
       if (e == cudaSuccess) {
@@ -300,6 +312,7 @@ struct pa_server_s {
         const int* cnt = pa::plan_timeout_counter(pe.plan);
         if (cnt) e = cudaMemcpyAsync(s.h_timeouts, cnt, sizeof(int), cudaMemcpyDeviceToHost, s.st);
       }
+      if (e == cudaSuccess && st == PA_OK) e = cudaEventRecord(s.ev_end, s.st);
       if (e == cudaSuccess && st == PA_OK) e = cudaEventRecord(s.ev, s.st);
       const double t = now();
       std::lock_guard<std::mutex> lk(mu);
@@ -504,6 +517,8 @@ pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
   for (auto& s : S->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_end);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_timeouts, sizeof(int));
     if (e == cudaSuccess) *s.h_timeouts = 0;
   }
@@ -512,6 +527,8 @@ pa_status pa_server_create(const pa_server_config* cfg, pa_server_t* out) {
     for (auto& s : S->slots) {
       if (s.st) cudaStreamDestroy(s.st);
       if (s.ev) cudaEventDestroy(s.ev);
+      if (s.ev_start) cudaEventDestroy(s.ev_start);
+      if (s.ev_end) cudaEventDestroy(s.ev_end);
       if (s.h_timeouts) cudaFreeHost(s.h_timeouts);
     }
     if (S->plan_stream) cudaStreamDestroy(S->plan_stream);
@@ -598,6 +615,7 @@ pa_status pa_server_wait(pa_server_t S, uint64_t ticket, int32_t timeout_ms,
   res->done_s = r->done;
   res->latency_ms = (r->done - r->arrival) * 1e3;
   res->batch_frames = r->batch;
+  res->device_ms = r->device_ms;
   S->by_ticket.erase(it);
   delete r;
   return PA_OK;
@@ -653,6 +671,8 @@ pa_status pa_server_destroy(pa_server_t S) {
     cudaStreamSynchronize(s.st);
     cudaStreamDestroy(s.st);
     cudaEventDestroy(s.ev);
+    cudaEventDestroy(s.ev_start);
+    cudaEventDestroy(s.ev_end);
     cudaFreeHost(s.h_timeouts);
   }
   cudaStreamDestroy(S->plan_stream);

@@ -30,6 +30,7 @@ class RequestResult(ctypes.Structure):
         ("done_s", ctypes.c_double),
         ("latency_ms", ctypes.c_double),
         ("batch_frames", ctypes.c_int32),
+        ("device_ms", ctypes.c_float),
     ]
 
     def as_dict(self):
