@@ -327,18 +327,23 @@ pa_status pa_plan_profile_read(pa_plan_t plan, double ms[3], int64_t launches[3]
  * it serves the paper's real-time use, Section 5, with many concurrent
  * frames of different geometries and orders).
  *
- * A server owns a scheduler thread, a cache of resident plans (delay tables
- * stay on the device between requests) and `slots` CUDA streams.  Each
- * request brings one RF frame in host memory and receives its output images
- * in host memory.  Whenever a slot is free the scheduler takes the oldest
- * request that has arrived, adds up to max_batch - 1 later arrivals with the
- * same descriptor, and runs them as one batch: RF copies, pa_beamform,
- * output copies, all on the slot's stream, so batches of different
- * requests overlap on the device.  A batch is admitted only when the device
- * memory it needs (its RF and output buffers, plus a new plan's tables) fits
- * in device_budget_bytes next to what is in flight; otherwise it waits.
- * Frames are independent and each pixel's arithmetic is fixed, so a result
- * is the same whichever batch it ran in.
+ * A server owns a scheduler thread, a plan-builder thread, a cache of
+ * resident plans (delay tables stay on the device between requests) and
+ * `slots` CUDA streams.  Each request brings one RF frame in host memory and
+ * receives its output images in host memory.  Whenever a slot is free the
+ * scheduler takes the oldest request that has arrived and whose plan is
+ * resident, adds up to max_batch - 1 later arrivals with the same
+ * descriptor, and runs them as one batch: RF copies, pa_beamform (kernel by
+ * kernel), output copies, all on the slot's stream, so batches of different
+ * requests overlap on the device.  A request with a new descriptor has its
+ * plan built on the builder thread (its own stream) while other requests go
+ * on; the plan's tables are admitted against the budget when the build
+ * starts.  A batch is admitted only when its RF and output buffers fit in
+ * device_budget_bytes next to what is in flight; otherwise it waits.  A
+ * compensated plan whose blocks could hold more tensor memory than their
+ * register share of an SM (pa_plan_info.tmem_dense) never runs together with
+ * another compensated batch.  Frames are independent and each pixel's
+ * arithmetic is fixed, so a result is the same whichever batch it ran in.
  * ---------------------------------------------------------------------- */
 typedef struct pa_server_s* pa_server_t;
 
