@@ -284,6 +284,69 @@ __device__ __forceinline__ void stockham_pass_inplace(float2* buf, int m, int ns
   team_sync<TW>(tm);
 }
 
+// The same pass over two buffers (the inverse transforms of both columns of
+// a pair): every team lane loads its groups of both, one barrier, then both
+// are transformed and stored - half the barriers of two separate passes and
+// twice the independent work between them.
+template <int R, int MPL, int TW>
+__device__ __forceinline__ void stockham_pass_inplace2(float2* bufa, float2* bufb, int m, int ns,
+                                                       const float2* twp, const Team& tm) {
+  constexpr int TL = 32 * TW;
+  constexpr int GPL = (32 * MPL / R) >= TL ? (32 * MPL / R) / TL : 1;
+  constexpr int PS = post_pad_shift(32 * MPL), PM = (1 << PS) - 1;
+  const int groups = m / R;
+  const int is = groups + (groups >> PS), os = ns + (ns >> PS);
+  const bool strided = (groups & PM) == 0 && (ns == 1 || (ns & PM) == 0);
+  float2 x[2][GPL][R];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const float2* buf = b ? bufb : bufa;
+#pragma unroll
+    for (int t = 0; t < GPL; ++t) {
+      const int j = tm.tl + TL * t;
+      if (j < groups) {
+        if (strided) {
+          const float2* ip = buf + pidx(j, PS);
+#pragma unroll
+          for (int r = 0; r < R; ++r) x[b][t][r] = ip[r * is];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) x[b][t][r] = buf[pidx(j + r * groups, PS)];
+        }
+      }
+    }
+  }
+  team_sync<TW>(tm);
+#pragma unroll
+  for (int t = 0; t < GPL; ++t) {
+    const int j = tm.tl + TL * t;
+    if (j < groups) {
+      const int k = j & (ns - 1);
+      float2 w[R];
+      if (ns > 1) twiddles<R>(twp, k, w);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        float2* buf = b ? bufb : bufa;
+        if (ns > 1) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) x[b][t][r] = cmul(x[b][t][r], w[r]);
+        }
+        dft_regs<R>(x[b][t]);
+        if (strided) {
+          float2* op = buf + pidx(base, PS);
+#pragma unroll
+          for (int r = 0; r < R; ++r) op[r * os] = x[b][t][r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) buf[pidx(base + r * ns, PS)] = x[b][t][r];
+        }
+      }
+    }
+  }
+  team_sync<TW>(tm);
+}
+
 // ---- k_post_inplace: 64 <= M <= 1024, two M-point buffers per team ----
 // Same algorithm as k_post below (pack two real columns, forward FFT, split
 // the spectra with the conjugate symmetry, mask, conjugate, forward FFT of
@@ -350,6 +413,37 @@ __device__ __forceinline__ void split_first_pass(float2* A, float2* B, const flo
                                                  const Team& tm) {
   using S = PostShape<MPL, TW>;
   constexpr int M = S::M, R = S::R1, PS = post_pad_shift(M);
+  if constexpr (2 * S::G1 <= S::TL) {
+    // fewer groups than half the team (1024 points: 64 radix-16 groups, 128
+    // lanes): lanes below G1 transform column a, the next G1 lanes column b
+    const bool colb = tm.tl >= S::G1;
+    const int j = colb ? tm.tl - S::G1 : tm.tl;
+    float2 x[R];
+    if (j < S::G1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = j + r * S::G1;
+        const float2 zn = A[pidx(n, PS)], zm = A[pidx((M - n) & (M - 1), PS)];
+        const float h = 0.5f * mk[n];
+        x[r] = colb ? make_float2(h * (zn.y + zm.y), h * (zn.x - zm.x))
+                    : make_float2(h * (zn.x + zm.x), -h * (zn.y - zm.y));
+      }
+      dft_any<R>(x);
+      if (colb) {
+        float2* op = B + pidx(R * j, PS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) op[r] = x[r];
+      }
+    }
+    team_sync<TW>(tm);  // every lane has read Z
+    if (!colb && j < S::G1) {
+      float2* op = A + pidx(R * j, PS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) op[r] = x[r];
+    }
+    team_sync<TW>(tm);
+    return;
+  }
   float2 xa[S::GPL][R];
 #pragma unroll
   for (int t = 0; t < S::GPL; ++t) {
@@ -422,6 +516,84 @@ __device__ __forceinline__ void last_pass_to_column(const float2* buf, const flo
   }
 }
 
+// Last pass of both inverse transforms: envelopes of columns a and b (b only
+// when the pair has two columns).
+template <int R, int MPL, int TW>
+__device__ __forceinline__ void last_pass_to_columns2(const float2* bufa, const float2* bufb,
+                                                      const float2* twp, float* cola, float* colb,
+                                                      int nz, float inv_m, float& mx,
+                                                      const Team& tm) {
+  constexpr int M = 32 * MPL, ns = M / R, groups = M / R, TL = 32 * TW;
+  constexpr int PS = post_pad_shift(M);
+  constexpr bool strided = (groups & ((1 << PS) - 1)) == 0;
+  constexpr int is = groups + (groups >> PS);
+#pragma unroll
+  for (int t = 0; t < (groups + TL - 1) / TL; ++t) {
+    const int j = tm.tl + TL * t;
+    if (j >= groups) break;
+    float2 x[2][R];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float2* buf = b ? bufb : bufa;
+      if constexpr (strided) {
+        const float2* ip = buf + pidx(j, PS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b][r] = ip[r * is];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b][r] = buf[pidx(j + r * groups, PS)];
+      }
+    }
+    float2 w[R];
+    twiddles<R>(twp, j, w);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[b][r] = cmul(x[b][r], w[r]);
+      dft_regs<R>(x[b]);
+      float* col = b ? colb : cola;
+      if (!col) continue;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = j + r * ns;
+        const float e = sqrtf(x[b][r].x * x[b][r].x + x[b][r].y * x[b][r].y) * inv_m;
+        if (n < nz) {
+          col[n] = e;
+          mx = fmaxf(mx, e);
+        }
+      }
+    }
+  }
+}
+
+// The inverse transforms of both columns after their fused first pass, pass
+// by pass together, the last pass writing both envelopes (colb null: the
+// pair's second column lies outside the image).
+template <int MPL, int TW>
+__device__ __forceinline__ void rest_passes2(float2* bufa, float2* bufb, const float2* tw,
+                                             float* cola, float* colb, int nz, float inv_m,
+                                             float& mx, const Team& tm) {
+  constexpr int M = 32 * MPL;
+  using S = PostShape<MPL, TW>;
+  int ns = S::R1, rem = S::LOG2 - S::LR1;
+  const float2* twp = tw;
+  while (rem > 0) {
+    const int lr = rem >= 3 ? 3 : rem;
+    if (lr == rem) {
+      if (lr == 3) last_pass_to_columns2<8, MPL, TW>(bufa, bufb, twp, cola, colb, nz, inv_m, mx, tm);
+      else if (lr == 2) last_pass_to_columns2<4, MPL, TW>(bufa, bufb, twp, cola, colb, nz, inv_m, mx, tm);
+      else last_pass_to_columns2<2, MPL, TW>(bufa, bufb, twp, cola, colb, nz, inv_m, mx, tm);
+      return;
+    }
+    if (lr == 3) stockham_pass_inplace2<8, MPL, TW>(bufa, bufb, M, ns, twp, tm);
+    else if (lr == 2) stockham_pass_inplace2<4, MPL, TW>(bufa, bufb, M, ns, twp, tm);
+    else stockham_pass_inplace2<2, MPL, TW>(bufa, bufb, M, ns, twp, tm);
+    twp += ns * ((1 << lr) - 1);
+    ns <<= lr;
+    rem -= lr;
+  }
+}
+
 // Passes after the first (twiddle blocks from the second pass on), the last
 // one writing the envelope; to_column = false keeps every pass in shared
 // memory (the forward transform).
@@ -481,8 +653,14 @@ __global__ void __launch_bounds__(256) k_post_inplace(const PostParams p) {
   // split + masks, first inverse pass of both columns
   split_first_pass<MPL, TW>(A, B, mk, tm);
   const float inv_m = 1.0f / (float)M;
-  rest_passes<MPL, TW>(A, tw, true, dst, p.nz, inv_m, mx, tm);
-  if (two) rest_passes<MPL, TW>(B, tw, true, dst + p.nz, p.nz, inv_m, mx, tm);
+  if constexpr (M == 1024) {
+    // both inverse transforms pass by pass together (registers stay at the
+    // kernel's 80; at 512 points they rose from 64 to 78, a block per SM)
+    rest_passes2<MPL, TW>(A, B, tw, dst, two ? dst + p.nz : nullptr, p.nz, inv_m, mx, tm);
+  } else {
+    rest_passes<MPL, TW>(A, tw, true, dst, p.nz, inv_m, mx, tm);
+    if (two) rest_passes<MPL, TW>(B, tw, true, dst + p.nz, p.nz, inv_m, mx, tm);
+  }
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
   if (lane == 0) atomicMax(p.maxslot + (size_t)f * p.n_out + o, __float_as_int(mx));
