@@ -4,8 +4,9 @@
 //
 // Delay tables: LATTICE (one entry per lattice offset and depth, shared by
 // the kC pairs of a thread at one channel step, see below) or FULL (one
-// 32-bit entry per pixel and element, Section 5's precomputed delays for any
-// grid); the FULL kernel reads kC entries per step, one per pair.
+// entry per pixel and element, Section 5's precomputed delays for any grid);
+// the FULL kernel reads kC entries per step, one per pair, as 32 contiguous
+// bytes.
 //
 // Work decomposition (one persistent CTA loop over work items):
 //   item   = (pixel tile, residue group, frame), taken from an atomic counter
@@ -590,18 +591,19 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     bool tsum_live = !LAZY;  // this item's totals are in TMEM
 
     // Table rows of this thread.  LATTICE: row t(u) = jt - dmin - m u at
-    // depth z.  FULL: the entry of pixel c (column jt + m c) and channel
-    // u + c sits at fbase0 + (u - u0) kC fcst + c fcst, the table being laid
-    // out per tile, step, pixel, row group, slot and row (the warp's 32
-    // entries of one step and pixel are contiguous).
+    // depth z.  FULL: the kC entries of step u (pixel c, column jt + m c,
+    // with channel u + c) are two 16-byte pairs, pixels 0-1 at fbase0 +
+    // (u - u0) fstep and pixels 2-3 half a step further (fhalf): per tile,
+    // step and half, the threads' pairs are contiguous.
     const int2* tcol = p.table + z;
     const float* wcol = APOD ? p.wtab + z : nullptr;
     const int row_u0 = jt - p.dmin;
     const int mstride = p.m * p.table_stride;
-    const size_t fcst = (size_t)32 * p.slots;
-    const size_t fbase0 = (size_t)tile_id * p.steps * kC * fcst +
-                          ((size_t)(warp / sg) * p.slots + sl) * (1 << lr_log2) +
-                          (lane & ((1 << lr_log2) - 1));
+    const size_t fhalf = (size_t)32 * p.slots * 2;
+    const size_t fstep = 2 * fhalf;
+    const size_t fbase0 = (size_t)tile_id * (p.steps + 3) * fstep +
+                          (((size_t)(warp / sg) * p.slots + sl) * (1 << lr_log2) +
+                           (lane & ((1 << lr_log2) - 1))) * 2;
 
     int lo_next = 0;  // window start of my channel in the next chunk to issue
     if (p.use_tma && vk.x < vk.y) {
@@ -667,24 +669,32 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
       if (u >= u_end) continue;
 
       if constexpr (FULL) {
-        // Packed entries [and weights] of the kC pairs of step uu.
-        auto load_step = [&](uint32_t (&e)[kC], float (&w)[kC], int uu) {
-          const size_t o = fbase0 + (size_t)(uu - p.u0) * kC * fcst;
+        // Entries [and weights] of the kC pairs of step uu: two 16-byte loads.
+        auto load_step = [&](int2 (&e)[kC], float (&w)[kC], int uu) {
+          const size_t o = fbase0 + (size_t)(uu - p.u0) * fstep;
 #ifdef PA_CHECK_BOUNDS
-          if (o + (kC - 1) * fcst >= (size_t)(tile_id + 1) * p.steps * kC * fcst) atomicOr(p.err, 1);
+          if (o + fhalf + 2 > (size_t)(tile_id + 1) * (p.steps + 3) * fstep) atomicOr(p.err, 1);
 #endif
-#pragma unroll
-          for (int c = 0; c < kC; ++c) {
-            e[c] = __ldg(p.ftab + o + c * fcst);
-            if constexpr (APOD) w[c] = __ldg(p.wtab + o + c * fcst);
+          const int4 q0 = __ldg(reinterpret_cast<const int4*>(p.ftab + o));
+          const int4 q1 = __ldg(reinterpret_cast<const int4*>(p.ftab + o + fhalf));
+          e[0] = make_int2(q0.x, q0.y);
+          e[1] = make_int2(q0.z, q0.w);
+          e[2] = make_int2(q1.x, q1.y);
+          e[3] = make_int2(q1.z, q1.w);
+          if constexpr (APOD) {
+            const float2 w0 = __ldg(reinterpret_cast<const float2*>(p.wtab + o));
+            const float2 w1 = __ldg(reinterpret_cast<const float2*>(p.wtab + o + fhalf));
+            w[0] = w0.x;
+            w[1] = w0.y;
+            w[2] = w1.x;
+            w[3] = w1.y;
           }
         };
-        // kC steps from uu.  The entries of the step after next are loaded
-        // while the current step is evaluated (two steps of latency cover);
-        // near the end of the chunk the last step's entries are reloaded
-        // instead of reading past it.
-        auto fblock = [&](auto near_tag, uint32_t (&e0)[kC], uint32_t (&e1)[kC],
-                          float (&w0)[kC], float (&w1)[kC], int uu) {
+        // kC steps from uu; the entries of the step after next are loaded
+        // while the current one is evaluated (the padding steps at the end
+        // of the tile's table keep those loads in bounds).
+        auto fblock = [&](auto near_tag, int2 (&e)[kC], int2 (&e1)[kC], float (&w)[kC],
+                          float (&w1)[kC], int uu) {
           constexpr bool NEAR = decltype(near_tag)::value;
           int cb[2 * kC];
           {
@@ -695,13 +705,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
           }
 #pragma unroll
           for (int tt = 0; tt < kC; ++tt) {
-            uint32_t e2[kC];
+            int2 e2[kC];
             float w2[kC];
-            load_step(e2, w2, min(uu + tt + 2, u_end - 1));
+            load_step(e2, w2, uu + tt + 2);
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
-              const uint32_t q = e0[c];
-              int addr = cb[tt + c] + (int)((q & 0x1ffu) << 3);
+              int addr = cb[tt + c] + e[c].x;
 #ifdef PA_CHECK_BOUNDS
               if (addr < pairs_off || addr > smem_hi) {
                 atomicOr(p.err, 2);
@@ -712,21 +721,19 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
               if constexpr (NEAR) {
                 asm volatile("ld.shared.f32 %0, [%1];" : "=f"(s) : "r"(addr));
               } else {
-                // 1 + a as an FP32 bit pattern: exponent 127 over the 23 bits of a
-                const float a = __uint_as_float(__funnelshift_r(q, 0x7fu, 9)) - 1.0f;
                 float2 r;
                 asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
-                s = fmaf(a, r.y, r.x);
+                s = fmaf(__int_as_float(e[c].y), r.y, r.x);
               }
-              if constexpr (APOD) s *= w0[c];
+              if constexpr (APOD) s *= w[c];
               pair_update<K>(acc[c], s);
             }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
-              e0[c] = e1[c];
+              e[c] = e1[c];
               e1[c] = e2[c];
               if constexpr (APOD) {
-                w0[c] = w1[c];
+                w[c] = w1[c];
                 w1[c] = w2[c];
               }
             }
@@ -739,13 +746,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
             }
           }
         };
-        uint32_t e0[kC], e1[kC];
-        float w0[kC], w1[kC];
-        load_step(e0, w0, u);
-        load_step(e1, w1, min(u + 1, u_end - 1));
+        int2 e[kC], e1[kC];
+        float w[kC], w1[kC];
+        load_step(e, w, u);
+        load_step(e1, w1, u + 1);
         for (; u < u_end; u += kC) {
-          if (p.nearest) fblock(std::true_type{}, e0, e1, w0, w1, u);
-          else fblock(std::false_type{}, e0, e1, w0, w1, u);
+          if (p.nearest) fblock(std::true_type{}, e, e1, w, w1, u);
+          else fblock(std::false_type{}, e, e1, w, w1, u);
         }
         continue;
       } else {

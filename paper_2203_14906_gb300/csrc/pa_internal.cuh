@@ -81,10 +81,10 @@ struct BfParams {  // aligned as CUtensorMap requires
   long long frame_elems;  // N * Ns
   const int2* table;      // lattice table [ndrows][nz_pad] {n0 * 8, float bits of a},
                           // rows = lattice offsets
-  const uint32_t* ftab;   // full table, in the kernel's read order: per tile,
-                          // channel step, pixel c, row group, slot, row; a in
-                          // bits 31..9 (2^-23 units), the slot n0 - window
-                          // start in bits 8..0
+  const int2* ftab;       // full table, in the kernel's read order: per tile,
+                          // channel step (steps + 3), pixel half c / 2, thread
+                          // of the tile, pixel c % 2: {(n0 - window start) * 8,
+                          // float bits of a}
   int full;               // 1: full table (channel bases are window starts)
   int steps;              // channel steps u1 - u0
   const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)

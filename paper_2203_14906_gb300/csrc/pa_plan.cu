@@ -68,7 +68,7 @@ struct pa_plan_s {
   int m = 1, R = 1, slots = 1, warps = 1, ngroups = 1, threads = 32;
   int tile_x = 0, tile_z = 32, nxt = 0, nzt = 0, n_tiles = 0, nx_pad = 0, nz_pad = 0;
   int u0 = 0, u1 = 0, nv = 0, dmin = 0, ndrows = 0, window = 0;
-  size_t full_entries = 0;  // entries of the full table (n_tiles * steps * kC * 32 * slots)
+  size_t full_entries = 0;  // entries of the full table (n_tiles * (steps + 3) * 32 * slots * kC)
   size_t smem = 0;
   int blocks_per_sm = 0;
   bool use_tma = false;
@@ -87,7 +87,7 @@ struct pa_plan_s {
   float dyn_range = 60.f;
   // device memory
   int2* table = nullptr;     // lattice table
-  uint32_t* ftab = nullptr;  // full table (packed entries, see k_table_full)
+  int2* ftab = nullptr;      // full table (see k_table_full)
   float* wtab = nullptr;
   int* lo = nullptr;
   int2* urange = nullptr;
@@ -168,29 +168,57 @@ namespace {
 
 // ---------------------------------------------------------- plan kernels
 // Layout of the full table, in the order the fused kernel reads it: per
-// tile, channel step u' = u - u0, pixel c of a thread, row group rg of the
-// tile's 32 rows, warp slot sl and row zl within the group:
-//   ((((tile * steps + u') * kC + c) * RG + rg) * slots + sl) * LR + zl
-// with LR depth rows per lane group and RG = 32 / LR.  The 32 lanes of a
-// warp (LR rows x 32 / LR neighbouring slots) read 128 contiguous bytes.
+// tile, channel step u' = u - u0 (steps + 3 of them: the last three are
+// padding, so the kernel loads two steps ahead with no bound check), half h
+// = c / 2 of a thread's kC = 4 pixels, thread t = (rg * slots + sl) * LR + zl
+// of the tile (row group rg of the tile's 32 rows, warp slot sl, row zl
+// within the group) and pixel c % 2:
+//   (((tile * (steps + 3) + u') * 2 + h) * (32 slots) + t) * 2 + c % 2
+// with LR depth rows per lane group and RG = 32 / LR.  A thread loads a step
+// as two 16-byte entries pairs; the 32 lanes of a warp read each of them as
+// 512 contiguous bytes.
 struct FullGeom {
   int nxt, n_tiles, tile_x, tile_z, m, slots, steps, lr_log2, nx, nz, n_elem, u0, nv;
 };
+
+static_assert(kC == 4, "the full table splits a thread's step into two entry pairs");
 
 __host__ __device__ __forceinline__ size_t full_index(const FullGeom& f, int tile, int up, int c,
                                                      int sl, int zt) {
   const int lr = 1 << f.lr_log2;
   const int rg = zt >> f.lr_log2, zl = zt & (lr - 1);
-  return ((((size_t)tile * f.steps + up) * kC + c) * (32 >> f.lr_log2) + rg) * f.slots * lr +
-         (size_t)sl * lr + zl;
+  const size_t threads = (size_t)32 * f.slots;
+  const size_t t = ((size_t)rg * f.slots + sl) * lr + zl;
+  return ((((size_t)tile * (f.steps + 3) + up) * 2 + (c >> 1)) * threads + t) * 2 + (c & 1);
+}
+
+// Entries of one tile in the full table.
+__host__ __device__ __forceinline__ size_t full_per_tile(const FullGeom& f) {
+  return (size_t)(f.steps + 3) * 32 * f.slots * kC;
+}
+
+// (step, pixel, slot, row in the tile) of entry e of a tile.
+__device__ __forceinline__ void full_decode(const FullGeom& f, size_t e, int* up, int* c, int* sl,
+                                            int* zt) {
+  const int lr = 1 << f.lr_log2;
+  const size_t threads = (size_t)32 * f.slots;
+  const int c_lo = (int)(e & 1);
+  size_t q = e >> 1;
+  const size_t t = q % threads;
+  q /= threads;
+  *c = (int)(q & 1) * 2 + c_lo;
+  *up = (int)(q >> 1);
+  const int zl = (int)(t % lr);
+  const size_t t2 = t / lr;
+  *sl = (int)(t2 % f.slots);
+  const int rg = (int)(t2 / f.slots);
+  *zt = rg * lr + zl;
 }
 
 // Pixel column of pixel c of warp slot sl in tile column tx.
 __host__ __device__ __forceinline__ int full_column(const FullGeom& f, int tx, int sl, int c) {
   return tx * f.tile_x + (sl / f.m) * f.m * kC + (sl % f.m) + f.m * c;
 }
-// Widest RF window (slots) the packed full-table entry addresses.
-constexpr int kFullMaxWindow = 512;
 
 struct TableGeom {
   int ndrows, nzp, dmin, ns, nearest;
@@ -266,39 +294,32 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
 
 // Full table: the entry of every (pixel, channel step) pair the fused kernel
 // evaluates (pixel c of slot sl pairs with channel u + c at step u), in the
-// layout of full_index, packed in 32 bits relative to the RF window its tile
-// stages for that channel (lo, from k_windows_full): bits 31..9 the fraction
-// a in 23 bits (truncated, so a < 1 stays below 1), bits 8..0 the slot
-// n0 - lo (the window is at most kFullMaxWindow slots wide).
-__global__ void k_table_full(TableGeom g, FullGeom f, const int* lo, uint32_t* table,
-                             float* wtab) {
+// layout of full_index: {(n0 - lo) * 8, FP32 bits of a}, the sample relative
+// to the RF window its tile stages for that channel (lo, from
+// k_windows_full) as a byte offset into the window's interpolation slots.
+// The padding steps hold zeros.
+__global__ void k_table_full(TableGeom g, FullGeom f, const int* lo, int2* table, float* wtab) {
   const int tile = blockIdx.y;
-  const size_t per_tile = (size_t)f.steps * kC * 32 * f.slots;
+  const size_t per_tile = full_per_tile(f);
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= per_tile) return;
-  const int lr = 1 << f.lr_log2;
-  size_t t = e;
-  const int zl = (int)(t % lr);
-  t /= lr;
-  const int sl = (int)(t % f.slots);
-  t /= f.slots;
-  const int rg = (int)(t % (32 >> f.lr_log2));
-  t /= (32 >> f.lr_log2);
-  const int c = (int)(t % kC);
-  const int up = (int)(t / kC);
+  int up, c, sl, zt;
+  full_decode(f, e, &up, &c, &sl, &zt);
+  const size_t ti = (size_t)tile * per_tile + e;
+  if (up >= f.steps) {
+    table[ti] = make_int2(0, 0);
+    if (wtab) wtab[ti] = 0.f;
+    return;
+  }
   const int tx = tile % f.nxt, tz = tile / f.nxt;
   const int j = full_column(f, tx, sl, c);
   const int v = up + c;
-  const int z = tz * f.tile_z + rg * lr + zl;
   const double dxv = full_dx(g, j, v);
-  const double zp = pixel_z(g, z);
+  const double zp = pixel_z(g, tz * f.tile_z + zt);
   int n0;
   double a;
   delay_sample(g, dxv, zp, &n0, &a);
-  const int off = n0 - lo[(size_t)tile * g.nv + v];
-  const uint32_t frac = (uint32_t)(a * 8388608.0);  // a * 2^23, a in [0, 1)
-  const size_t ti = (size_t)tile * per_tile + e;
-  table[ti] = (frac << 9) | (uint32_t)(off & 0x1ff);
+  table[ti] = make_int2((n0 - lo[(size_t)tile * g.nv + v]) * 8, __float_as_int((float)a));
   if (wtab) wtab[ti] = apod_weight(g, dxv, zp);
 }
 
@@ -306,24 +327,16 @@ __global__ void k_table_full(TableGeom g, FullGeom f, const int* lo, uint32_t* t
 // and elements only).
 __global__ void k_count_active_full(FullGeom f, const float* wtab, unsigned long long* count) {
   const int tile = blockIdx.y;
-  const size_t per_tile = (size_t)f.steps * kC * 32 * f.slots;
+  const size_t per_tile = full_per_tile(f);
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long cnt = 0;
   if (e < per_tile) {
-    const int lr = 1 << f.lr_log2;
-    size_t t = e;
-    const int zl = (int)(t % lr);
-    t /= lr;
-    const int sl = (int)(t % f.slots);
-    t /= f.slots;
-    const int rg = (int)(t % (32 >> f.lr_log2));
-    t /= (32 >> f.lr_log2);
-    const int c = (int)(t % kC);
-    const int up = (int)(t / kC);
+    int up, c, sl, zt;
+    full_decode(f, e, &up, &c, &sl, &zt);
     const int j = full_column(f, tile % f.nxt, sl, c);
-    const int z = (tile / f.nxt) * f.tile_z + rg * lr + zl;
+    const int z = (tile / f.nxt) * f.tile_z + zt;
     const int i = up + c + f.u0;
-    if (j < f.nx && z < f.nz && i >= 0 && i < f.n_elem &&
+    if (up < f.steps && j < f.nx && z < f.nz && i >= 0 && i < f.n_elem &&
         wtab[(size_t)tile * per_tile + e] > 0.f)
       cnt = 1;
   }
@@ -617,7 +630,7 @@ void configure(pa_plan_s* P) {
   if (P->full) {  // one entry per evaluated (pixel, channel step) pair
     P->dmin = 0;
     P->ndrows = 0;
-    P->full_entries = (size_t)P->n_tiles * steps * kC * 32 * P->slots;
+    P->full_entries = (size_t)P->n_tiles * (steps + 3) * 32 * P->slots * kC;
   } else {
     P->dmin = -P->m * i_max;
     const int dmax = P->nx_pad - 1 + P->m * (kC - 1);
@@ -704,7 +717,7 @@ cudaError_t fused_blocks_per_sm(const pa_plan_s* P, size_t smem, int* n) {
 
 // Bytes of the delay table and its apodisation weights.
 size_t delay_table_bytes(const pa_plan_s* P) {
-  if (P->full) return P->full_entries * (sizeof(uint32_t) + (P->apod ? sizeof(float) : 0));
+  if (P->full) return P->full_entries * (sizeof(int2) + (P->apod ? sizeof(float) : 0));
   return (size_t)P->ndrows * P->nz_pad * (sizeof(int2) + (P->apod ? sizeof(float) : 0));
 }
 
@@ -920,11 +933,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   if (head[0] != 0) return fail(PA_ECUDA, "plan build: table row outside range (flag %d)", head[0]);
   const int width = head[2];
   P->window = ((std::max(width, 1) + 3) / 4) * 4;
-  if (P->full && P->window > kFullMaxWindow)
-    return fail(PA_EUNSUPPORTED,
-                "RF window of %d samples per channel exceeds the %d the full delay table "
-                "addresses; use a finer depth grid",
-                P->window, kFullMaxWindow);
+
   PA_CUDA(cudaMemsetAsync(P->scratch[0], 0, P->scratch_ints * sizeof(int), st));
 
   // TMA box geometry of one staged channel
