@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--launches", type=int, default=3, help="--case: timed launches")
     ap.add_argument("--table", default="auto", choices=["auto", "lattice", "full"],
                     help="--case: delay-table form")
+    ap.add_argument("--interp", default="linear", choices=["linear", "nearest"],
+                    help="--case: sampling of the delayed signal")
     args = ap.parse_args()
     if args.case is None:
         args.frames = 32 if args.frames is None else args.frames
@@ -1047,7 +1049,7 @@ def run_case(args):
     import paper_2203_14906_gb300 as pa
 
     over = {kk: v for kk, v in (("nx", args.nx), ("nz", args.nz)) if v is not None}
-    wl = synth.workload(args.case, delay_table=args.table, **over)
+    wl = synth.workload(args.case, delay_table=args.table, interp=args.interp, **over)
     F = args.frames or int(wl.get("n_frames", 1))
     k = args.order or int(wl.get("order_k", 3))
     rf_dtype = args.rf or wl.get("rf_dtype", "f32")
@@ -1077,7 +1079,7 @@ def run_case(args):
         info = plan.info()
     print(json.dumps({
         "case": args.case, "grid": [wl["nx"], wl["nz"]], "frames": F, "order_k": k,
-        "rf": rf_dtype, "compensated": comp,
+        "rf": rf_dtype, "compensated": comp, "interp": args.interp,
         "kernels_ms_per_launch": {kk: v[0] / max(v[1], 1) for kk, v in prof.items()},
         "plan": {f: info[f] for f in LAUNCH_FIELDS + ("lattice_m", "tmem_columns", "delay_table",
                                                       "table_bytes")},
