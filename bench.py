@@ -75,6 +75,9 @@ def parse():
                     help="--case: delay-table form")
     ap.add_argument("--interp", default="linear", choices=["linear", "nearest"],
                     help="--case: sampling of the delayed signal")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 32],
+                    help="--case: time the channels-on-lanes mapping (pa_lanes_raw) with this "
+                         "many lanes per pixel instead of the launch sequence")
     args = ap.parse_args()
     if args.case is None:
         args.frames = 32 if args.frames is None else args.frames
@@ -1004,6 +1007,9 @@ def run_ours(args):
         }
         extras["off_lattice_form"] = off_lattice_bench(pa, torch, args, stream, flush, peak,
                                                        value / ws)
+        if args.order == 3 and rank == 0:
+            extras["mapping_comparison"] = mapping_bench(pa, torch, args, wl, frames64, stream,
+                                                         flush, bf_s * 1e3, peak)
         if rank == 0:
             nrep = min(8, frames64.shape[0])
             extras["precision_report"] = {
@@ -1040,6 +1046,62 @@ def run_ours(args):
     return 0
 
 
+def lanes_times(pa, torch, plan, rf, F, lanes, warmup, launches, stream, flush):
+    """CUDA-event times (s) of pa_lanes_raw launches, an L2 flush before each."""
+    from paper_2203_14906_gb300 import _native
+
+    L = _native.load()
+    out = torch.empty(plan.out_shape(F, pa.PA_STAGE_RAW), dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(launches)]
+    with torch.cuda.stream(stream):
+        for i in range(warmup + launches):
+            flush()
+            if i >= warmup:
+                evs[i - warmup][0].record(stream)
+            st = L.pa_lanes_raw(plan.handle, rf.data_ptr(), F, out.data_ptr(), lanes,
+                                stream.cuda_stream)
+            if st != 0:
+                raise RuntimeError(L.pa_last_error().decode())
+            if i >= warmup:
+                evs[i - warmup][1].record(stream)
+        stream.synchronize()
+    return [a.elapsed_time(b) / 1e3 for a, b in evs]
+
+
+def run_case_lanes(args, pa, torch, wl, F, k, rf, desc, stream, flush):
+    with pa.Plan(desc, stream=stream) as plan:
+        t = lanes_times(pa, torch, plan, rf, F, args.lanes, args.warmup, args.launches, stream,
+                        lambda: flush.zero_())
+    print(json.dumps({"case": args.case, "grid": [wl["nx"], wl["nz"]], "frames": F,
+                      "order_k": k, "lanes_per_pixel": args.lanes,
+                      "k_lanes_ms_per_launch": float(np.mean(t)) * 1e3}), flush=True)
+    return 0
+
+
+def mapping_bench(pa, torch, args, wl, frames64, stream, flush, fused_ms, peak):
+    """The channels-on-lanes mapping (pa_lanes_raw, 4 / 8 / 32 lanes per
+    pixel, partial sums added by warp shuffles) against the fused kernel's
+    pixels-on-lanes mapping, on the headline workload's frames (FP32, k = 3,
+    RAW planes), device-timed with an L2 flush before each launch."""
+    import synth
+
+    F = frames64.shape[0]
+    store, _ = synth.quantize(frames64, "f32")
+    rf = torch.from_numpy(store).cuda()
+    out = {"workload": "headline frames, FP32, k = 3, raw sums only",
+           "fused_kernel_ms": fused_ms}
+    desc = pa.make_desc(wl, order_k=3, outputs=7, rf_dtype="f32", max_batch=F)
+    pairs = wl["nx"] * wl["nz"] * wl["n_elem"] * F
+    with pa.Plan(desc, stream=stream) as plan:
+        for lanes in (4, 8, 32):
+            t = float(np.mean(lanes_times(pa, torch, plan, rf, F, lanes, 3, 10, stream, flush)))
+            out[f"lanes_{lanes}"] = {
+                "kernel_ms": t * 1e3, "vs_fused": fused_ms / (t * 1e3),
+                "frac": pairs * ops_per_pair(3) / t / 1e12 / peak}
+    return out
+
+
 def run_case(args):
     """One workload's launch sequence, timed per kernel (see the module
     docstring); no oracle, no extras."""
@@ -1062,6 +1124,8 @@ def run_case(args):
     x = torch.randn(F, wl["n_elem"], wl["n_samples"], device=dev, generator=g)
     rf = x.to({"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[rf_dtype])
     desc = pa.make_desc(wl, order_k=k, outputs=7, rf_dtype=rf_dtype, max_batch=F, compensated=comp)
+    if args.lanes:
+        return run_case_lanes(args, pa, torch, wl, F, k, rf, desc, stream, flush)
     with pa.Plan(desc, stream=stream) as plan, torch.cuda.stream(stream):
         out = torch.empty(plan.out_shape(F, pa.PA_STAGE_LOG), dtype=torch.float32, device=dev)
         for _ in range(args.warmup):

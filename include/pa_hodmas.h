@@ -517,6 +517,20 @@ pa_status pa_log_compress_noalloc(const float* env_dev, int32_t n_images,
                                   int64_t image_elems, float dyn_range_db,
                                   float* log_dev, void* cuda_stream);
 
+/*
+ * pa_lanes_raw -- the other thread mapping of the fused pass, kept for
+ * measurement (not the product path): channels on lanes, lanes_per_pixel
+ * (4, 8 or 32) lanes per pixel, each lane's DAS / DMAS / DMAS-3 sums added
+ * across the pixel's lanes by warp shuffles before the epilogue (Eq. 3,
+ * Eq. 7).  Writes the RAW planes of n_frames frames (layout of pa_beamform
+ * with stages = PA_STAGE_RAW) for a plan in the plain FP32 lattice form at
+ * k = 3 (else PA_EUNSUPPORTED); n_frames <= the plan's max_batch.  Results
+ * agree with pa_beamform's RAW planes to FP32 rounding (channel sums are
+ * added in another order).  Asynchronous on cuda_stream.
+ */
+pa_status pa_lanes_raw(pa_plan_t plan, const void* rf_dev, int32_t n_frames, float* out_dev,
+                       int32_t lanes_per_pixel, void* cuda_stream);
+
 const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);

@@ -46,6 +46,7 @@ EXPORTS = (
     "pa_status_str",
     "pa_last_error",
     "pa_version",
+    "pa_lanes_raw",
 )
 
 
@@ -218,6 +219,8 @@ def load(checked: bool = False, build: bool = True):
         L.pa_beamform.restype = ctypes.c_int
         L.pa_beamform_host.argtypes = [vp, vp, i32, vp, u32, vp]
         L.pa_beamform_host.restype = ctypes.c_int
+        L.pa_lanes_raw.argtypes = [vp, vp, i32, vp, i32, vp]
+        L.pa_lanes_raw.restype = ctypes.c_int
         L.pa_plan_use_graph.argtypes = [vp, i32]
         L.pa_plan_use_graph.restype = ctypes.c_int
         L.pa_plan_profile.argtypes = [vp, i32]

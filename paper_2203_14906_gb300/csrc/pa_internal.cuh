@@ -196,6 +196,11 @@ void set_error_message(const char* msg);
 int* plan_timeout_counter(pa_plan_s* P);
 // Device memory the plan owns (without synchronising, unlike pa_plan_get_info).
 size_t plan_device_bytes(const pa_plan_s* P);
+// The fused kernel's parameters for one launch of nf frames (what pa_beamform
+// would launch), the plan's order, and whether the plan is the plain FP32
+// lattice form with linear interpolation.
+pa_status plan_bf_params(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                         BfParams* b, int* k, bool* lattice_fp32_plain);
 // TMEM columns per fused-kernel block and whether the plan is TMEM-dense
 // (its blocks can hold more TMEM than their register share of an SM).
 void plan_tmem(const pa_plan_s* P, int* cols, bool* dense);

@@ -1597,6 +1597,18 @@ int* plan_timeout_counter(pa_plan_s* P) {
 
 size_t plan_device_bytes(const pa_plan_s* P) { return P ? P->device_bytes : 0; }
 
+pa_status plan_bf_params(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
+                         BfParams* b, int* k, bool* lattice_fp32_plain) {
+  ChunkLaunch c;
+  const pa_status s = prepare_chunk(P, rf, nf, out, stages, P->scratch[0], &c);
+  if (s != PA_OK) return s;
+  *b = c.b;
+  *k = P->K;
+  *lattice_fp32_plain = !P->full && !P->apod && !P->comp && P->d.rf_dtype == PA_RF_F32 &&
+                        P->d.interp == PA_INTERP_LINEAR;
+  return PA_OK;
+}
+
 // A compensated plan's fused-kernel blocks hold tmem_cols TMEM columns each.
 // Whatever blocks share an SM, their registers add up to at most the SM's
 // register file, so if every block's columns are within its register share

@@ -612,3 +612,32 @@ def test_full_table_checked_build():
         rf = synth.make_frame(wl, 1)[None]
         _, info, _ = run_gpu(wl, rf, k, rf_dtype=dt, compensated=comp, checked=True)
         assert info["device_error_flags"] == 0 and info["delay_table"] == 2, (wl["nx"], k)
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 32])
+def test_channel_lanes_mapping_matches_fused(lanes):
+    """The channels-on-lanes mapping (kept for measurement) computes the
+    same RAW images as the fused kernel, to FP32 rounding (its channel sums
+    are added in another order)."""
+    import ctypes
+
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+    from paper_2203_14906_gb300 import _native
+
+    for name in ("cfg1", "cfg2"):
+        wl = synth.workload(name)
+        F = 2
+        rf = torch.from_numpy(synth.quantize(_frames(wl, [3, 4]), "f32")[0]).cuda()
+        with pa.Plan(pa.make_desc(wl, order_k=3, max_batch=F)) as plan:
+            want = pa.beamform(plan, rf, 1)
+            got = torch.full_like(want, 7.0)
+            L = _native.load()
+            st = L.pa_lanes_raw(plan._h, rf.data_ptr(), F, got.data_ptr(), lanes,
+                                torch.cuda.current_stream().cuda_stream)
+            assert st == 0, L.pa_last_error()
+            torch.cuda.synchronize()
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        peak = np.max(np.abs(w), axis=(-2, -1), keepdims=True)
+        assert np.max(np.abs(w - g) / peak) <= 1e-5, (name, lanes)
