@@ -307,8 +307,10 @@ pa_status pa_pipe_schedule(const pa_pipe_model* model, int32_t n_frames, int32_t
  * (clear, fused beamforming kernel, post-filter, log) runs as one CUDA graph;
  * the plan keeps one executable graph per (frames per launch, stages) and
  * only rewrites its buffer pointers on later calls.  enable = 0 launches the
- * kernels one by one.  Results are identical either way.  While kernel
- * timing is on (pa_plan_profile) kernels are launched one by one.
+ * kernels one by one.  Results are identical either way.  Kernel timing
+ * (pa_plan_profile) works in both modes: in graph mode the timed launches
+ * run a graph of their own with an event-record node before and after each
+ * kernel.
  */
 pa_status pa_plan_use_graph(pa_plan_t plan, int32_t enable);
 
@@ -316,6 +318,9 @@ pa_status pa_plan_use_graph(pa_plan_t plan, int32_t enable);
  * Kernel timing.  While enabled, every launch of the plan's kernels is
  * bracketed by CUDA events recorded on the stream it runs on (kernel kinds:
  * 0 fused beamforming, 1 post-filter/envelope, 2 log compression).
+ * enable: 0 off, 1 every kernel, 2 the fused beamforming kernel only (each
+ * timed kernel adds two event records, which stop the next launch from
+ * overlapping the previous kernel's tail); other values: PA_EINVAL.
  * pa_plan_profile_read waits for the recorded events, returns the summed
  * milliseconds and launch counts per kind and clears them.
  */

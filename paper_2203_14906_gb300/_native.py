@@ -356,9 +356,11 @@ class Plan:
         """Launch each sequence as a CUDA graph (default) or kernel by kernel."""
         check(self._L, self._L.pa_plan_use_graph(self._h, int(bool(enable))))
 
-    def profile(self, enable: bool = True):
-        """Record CUDA events around each of this plan's kernel launches."""
-        check(self._L, self._L.pa_plan_profile(self._h, int(bool(enable))))
+    def profile(self, enable: bool = True, fused_only: bool = False):
+        """Record CUDA events around each of this plan's kernel launches (or,
+        with fused_only, around the fused beamforming kernel's alone)."""
+        mode = 0 if not enable else (2 if fused_only else 1)
+        check(self._L, self._L.pa_plan_profile(self._h, mode))
 
     def profile_read(self):
         """{kernel: (total_ms, launches)} since the last read; synchronises."""

@@ -150,12 +150,16 @@ struct pa_plan_s {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t n_memset = nullptr;  // clearing kernel
     cudaGraphNode_t n_bf = nullptr, n_post = nullptr, n_log = nullptr;
+    // timing graphs (built while pa_plan_profile is on): an event-record
+    // node before and after each kernel, given fresh events every launch
+    uint32_t prof = 0;  // kernel kinds timed (bit per kind)
+    cudaGraphNode_t n_ev[3][2] = {};
   };
   std::vector<GraphEntry> graphs;
   bool use_graph = true;
   int lane_rows_log2 = 5;  // depth rows per lane group of the fused kernel (log2)
-  // kernel timing (pa_plan_profile)
-  bool prof = false;
+  // kernel timing (pa_plan_profile): bit k set = kernel kind k is timed
+  uint32_t prof = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   // facts
@@ -1086,6 +1090,26 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
 
 int stage_index(uint32_t stages, uint32_t stage) { return popcount3(stages & (stage - 1u)); }
 
+// A timing event pair from the plan's free list (created when it is empty).
+bool take_events(pa_plan_s* P, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+  if (!P->ev_free.empty()) {
+    *ev = P->ev_free.back();
+    P->ev_free.pop_back();
+    return true;
+  }
+  *ev = {nullptr, nullptr};
+  if (cudaEventCreate(&ev->first) != cudaSuccess) {
+    ev->first = nullptr;
+    return false;
+  }
+  if (cudaEventCreate(&ev->second) != cudaSuccess) {
+    cudaEventDestroy(ev->first);
+    *ev = {nullptr, nullptr};
+    return false;
+  }
+  return true;
+}
+
 // Event pair around one kernel launch when timing is enabled.
 struct ProfScope {
   pa_plan_s* P;
@@ -1093,15 +1117,8 @@ struct ProfScope {
   cudaStream_t st;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   ProfScope(pa_plan_s* p, int k, cudaStream_t s) : P(p), kind(k), st(s) {
-    if (!P->prof) return;
-    if (!P->ev_free.empty()) {
-      ev = P->ev_free.back();
-      P->ev_free.pop_back();
-    } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
-               cudaEventCreate(&ev.second) != cudaSuccess) {
-      ev = {nullptr, nullptr};
-      return;
-    }
+    if (!(P->prof >> kind & 1u)) return;
+    if (!take_events(P, &ev)) return;
     cudaEventRecord(ev.first, st);
   }
   ~ProfScope() {
@@ -1281,12 +1298,15 @@ cudaKernelNodeParams node_params(const LaunchSpec& s, void** args) {
 
 
 // One chunk as a CUDA graph: clear -> fused kernel [-> post [-> log]].  An
-// executable graph is kept per (frames, stages); later calls only rewrite the
-// node parameters (buffer pointers) and launch it.
+// executable graph is kept per (frames, stages, timing); later calls only
+// rewrite the node parameters (buffer pointers, and the timing events) and
+// launch it.  While timing is on, each kernel node sits between two
+// event-record nodes, so the kernels are timed on the path that serves.
 pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cudaStream_t st) {
+  const uint32_t prof = P->prof;
   pa_plan_s::GraphEntry* ge = nullptr;
   for (auto& g : P->graphs)
-    if (g.nf == nf && g.stages == stages) ge = &g;
+    if (g.nf == nf && g.stages == stages && g.prof == prof) ge = &g;
   void* ab[] = {&c.b};
   void* aq[] = {&c.q};
   void* al[] = {&c.l};
@@ -1300,6 +1320,23 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
   const cudaKernelNodeParams kb = node_params(c.sb, ab);
   const cudaKernelNodeParams kq = node_params(c.sq, aq);
   const cudaKernelNodeParams kl = node_params(c.sl, al);
+  const bool has[3] = {true, c.post, c.log};
+  bool timed[3];
+  for (int k = 0; k < 3; ++k) timed[k] = has[k] && (prof >> k & 1u);
+  std::pair<cudaEvent_t, cudaEvent_t> ev[3] = {};
+  if (prof) {
+    for (int k = 0; k < 3; ++k) {
+      if (timed[k] && !take_events(P, &ev[k])) {
+        for (int j = 0; j < k; ++j)
+          if (ev[j].first) P->ev_free.push_back(ev[j]);
+        return fail(PA_ECUDA, "timing events: out of resources");
+      }
+    }
+  }
+  auto give_back = [&]() {
+    for (int k = 0; k < 3; ++k)
+      if (ev[k].first) P->ev_free.push_back(ev[k]);
+  };
   if (!ge) {
     // bounded cache: drop the oldest graph once 32 shapes are held (callers
     // that vary the batch size every call would otherwise grow it forever)
@@ -1311,20 +1348,35 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
     pa_plan_s::GraphEntry g;
     g.nf = nf;
     g.stages = stages;
+    g.prof = prof;
     cudaGraph_t graph;
-    PA_CUDA(cudaGraphCreate(&graph, 0));
-    cudaGraphNode_t prev;
-    cudaError_t e = cudaGraphAddKernelNode(&g.n_memset, graph, nullptr, 0, &kz);
-    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g.n_bf, graph, &g.n_memset, 1, &kb);
-    prev = g.n_bf;
-    if (e == cudaSuccess && c.post) {
-      e = cudaGraphAddKernelNode(&g.n_post, graph, &prev, 1, &kq);
-      prev = g.n_post;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) {
+      give_back();
+      return fail(PA_ECUDA, "graph build: %s", cudaGetErrorString(e));
     }
-    if (e == cudaSuccess && c.log) e = cudaGraphAddKernelNode(&g.n_log, graph, &prev, 1, &kl);
+    const cudaKernelNodeParams* kp[3] = {&kb, &kq, &kl};
+    cudaGraphNode_t* kn[3] = {&g.n_bf, &g.n_post, &g.n_log};
+    e = cudaGraphAddKernelNode(&g.n_memset, graph, nullptr, 0, &kz);
+    cudaGraphNode_t prev = g.n_memset;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      if (!has[k]) continue;
+      if (timed[k]) {
+        e = cudaGraphAddEventRecordNode(&g.n_ev[k][0], graph, &prev, 1, ev[k].first);
+        prev = g.n_ev[k][0];
+      }
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(kn[k], graph, &prev, 1, kp[k]);
+      if (e != cudaSuccess) break;
+      prev = *kn[k];
+      if (timed[k]) {
+        e = cudaGraphAddEventRecordNode(&g.n_ev[k][1], graph, &prev, 1, ev[k].second);
+        prev = g.n_ev[k][1];
+      }
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
     if (e != cudaSuccess) {
       cudaGraphDestroy(graph);
+      give_back();
       return fail(PA_ECUDA, "graph build: %s", cudaGetErrorString(e));
     }
     g.graph = graph;
@@ -1332,24 +1384,38 @@ pa_status launch_graph(pa_plan_s* P, ChunkLaunch& c, int nf, uint32_t stages, cu
     P->graphs.push_back(g);
     ge = &P->graphs.back();
   } else {
-    PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_memset, &kz));
-    PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_bf, &kb));
-    if (c.post) PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_post, &kq));
-    if (c.log) PA_CUDA(cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_log, &kl));
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_memset, &kz);
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_bf, &kb);
+    if (e == cudaSuccess && c.post)
+      e = cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_post, &kq);
+    if (e == cudaSuccess && c.log) e = cudaGraphExecKernelNodeSetParams(ge->exec, ge->n_log, &kl);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      if (!timed[k]) continue;
+      e = cudaGraphExecEventRecordNodeSetEvent(ge->exec, ge->n_ev[k][0], ev[k].first);
+      if (e == cudaSuccess)
+        e = cudaGraphExecEventRecordNodeSetEvent(ge->exec, ge->n_ev[k][1], ev[k].second);
+    }
+    if (e != cudaSuccess) {
+      give_back();
+      return fail(PA_ECUDA, "graph update: %s", cudaGetErrorString(e));
+    }
   }
-  PA_CUDA(cudaGraphLaunch(ge->exec, st));
+  const cudaError_t e = cudaGraphLaunch(ge->exec, st);
+  if (e != cudaSuccess) {
+    give_back();
+    return fail(PA_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+  }
+  for (int k = 0; k < 3; ++k)
+    if (ev[k].first) P->ev_used.push_back({k, ev[k]});
   return PA_OK;
 }
 
-// One launch sequence for nf <= max_batch frames.  Kernel timing needs the
-// direct launches (events bracket each kernel); otherwise the plan's graphs
-// are used when enabled.
 pa_status run_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32_t stages,
                     cudaStream_t st, int* scratch) {
   ChunkLaunch c;
   pa_status ps = prepare_chunk(P, rf, nf, out, stages, scratch, &c);
   if (ps != PA_OK) return ps;
-  if (P->use_graph && !P->prof) return launch_graph(P, c, nf, stages, st);
+  if (P->use_graph) return launch_graph(P, c, nf, stages, st);
   return launch_direct(P, c, st);
 }
 
@@ -1844,7 +1910,7 @@ pa_status pa_beamform_host(pa_plan_t P, const void* rf_host, int32_t n_frames, f
       PA_CUDA(cudaMemset(P->scratch[b], 0, P->scratch_ints * sizeof(int)));
     }
   }
-  if (P->use_graph && !P->prof && is_pinned(rf_host) && is_pinned(out_host)) {
+  if (P->use_graph && P->prof == 0 && is_pinned(rf_host) && is_pinned(out_host)) {
     // pinned buffers: the whole call is one graph launch on the caller's stream
     pa_plan_s::HostGraph* hg = nullptr;
     for (auto& g : P->host_graphs)
@@ -1950,7 +2016,8 @@ pa_status pa_plan_use_graph(pa_plan_t P, int32_t enable) {
 
 pa_status pa_plan_profile(pa_plan_t P, int32_t enable) {
   if (!P) return fail(PA_EINVAL, "null plan");
-  P->prof = enable != 0;
+  if (enable < 0 || enable > 2) return fail(PA_EINVAL, "profile mode %d not in 0..2", (int)enable);
+  P->prof = enable == 0 ? 0u : enable == 1 ? 7u : 1u;
   return PA_OK;
 }
 

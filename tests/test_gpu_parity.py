@@ -321,6 +321,50 @@ def test_graph_launch_matches_direct_launch():
     assert torch.equal(direct[1:], g3)
 
 
+def test_kernel_timing_in_both_launch_modes():
+    """Kernel timing works on the graph path (event-record nodes around each
+    kernel) and kernel by kernel: one timed launch per kernel per call, the
+    same bits as untimed launches, and timed graphs kept apart from the
+    untimed ones."""
+    import torch
+
+    import paper_2203_14906_gb300 as pa
+
+    wl = synth.workload("cfg1")
+    rf = torch.from_numpy(synth.quantize(_frames(wl, [4, 5, 6]), "f32")[0]).cuda()
+    with pa.Plan(pa.make_desc(wl, order_k=3, max_batch=3)) as plan:
+        ref = pa.beamform(plan, rf, 7)
+        for graph in (True, False):
+            plan.use_graph(graph)
+            plan.profile(True)
+            outs = [pa.beamform(plan, rf, 7) for _ in range(3)]
+            outs.append(pa.beamform(plan, rf, 3))  # no log stage
+            prof = plan.profile_read()
+            plan.profile(False)
+            assert prof["bf_fused"][1] == 4 and prof["post"][1] == 4, (graph, prof)
+            assert prof["log"][1] == 3, (graph, prof)
+            assert all(v[0] > 0.0 for v in prof.values()), (graph, prof)
+            for o in outs[:3]:
+                assert torch.equal(o, ref)
+            assert torch.equal(outs[3], ref[:, :2])  # stages raw + envelope
+            # the fused kernel alone
+            plan.profile(True, fused_only=True)
+            o = pa.beamform(plan, rf, 7)
+            prof = plan.profile_read()
+            plan.profile(False)
+            assert prof["bf_fused"][1] == 1 and prof["bf_fused"][0] > 0.0, (graph, prof)
+            assert prof["post"][1] == 0 and prof["log"][1] == 0, (graph, prof)
+            assert torch.equal(o, ref)
+        plan.use_graph(True)
+        again = pa.beamform(plan, rf, 7)
+        assert plan.profile_read()["bf_fused"][1] == 0
+        assert torch.equal(again, ref)
+        from paper_2203_14906_gb300._native import check
+
+        with pytest.raises(pa.PAError):
+            check(plan._L, plan._L.pa_plan_profile(plan._h, 3))
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_tma_and_load_staging_agree(dtype, monkeypatch):
     """Both RF staging paths (TMA boxes, vectorised loads) give the same bits."""
