@@ -494,8 +494,9 @@ struct TmemSums {
 
 // Resident 256-thread blocks per SM the register allocation targets: four
 // (64 registers) for plain orders <= 3, three (80 registers) for compensated
-// orders <= 3 (at 64 registers their TMEM traffic spills: 0.707 vs 0.676 ms)
-// and for orders 4-5, two for orders >= 6.
+// orders <= 3 (at 64 registers, four blocks per SM, they spill: cfg2 k = 3
+// BF16 0.717 ms with TMA staging and 0.750 ms with loads, against 0.663 ms
+// at 80) and for orders 4-5, two for orders >= 6.
 #ifndef PA_MINB4_MAX_K
 #define PA_MINB4_MAX_K 3
 #endif
