@@ -572,8 +572,11 @@ void configure(pa_plan_s* P) {
   const int lm = lattice_m(d);
   P->full = d.delay_table == PA_TABLE_FULL || (d.delay_table == PA_TABLE_AUTO && lm == 0);
   // 32-column tiles halve the staged samples per pair; small images keep
-  // 16-column tiles so that there are enough tiles to fill the GPU.
-  const bool big = (int64_t)d.nx * d.nz >= 512 * 512;
+  // 16-column tiles so that there are enough tiles to fill the GPU, unless a
+  // full launch (max_batch frames) holds at least 1024 32 x 32 tiles.
+  const int64_t wide_tiles =
+      (int64_t)((d.nx + 31) / 32) * ((d.nz + 31) / 32) * std::max(1, d.max_batch);
+  const bool big = (int64_t)d.nx * d.nz >= 512 * 512 || wide_tiles >= 1024;
   if (P->full) {
     // No table entry is shared, so the column stride m of a thread's pixels
     // is free: 4 (as the lattice has at cfg2) keeps a warp's slots on

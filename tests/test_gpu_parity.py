@@ -74,6 +74,28 @@ def test_ragged_grid_odd_aperture_unaligned_samples():
         assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"ragged k={k}")
 
 
+@pytest.mark.parametrize("k,dtype", [(3, "f32"), (2, "f32"), (5, "bf16")])
+def test_small_grid_in_a_large_batch_takes_wide_tiles(k, dtype):
+    """A 128 x 128 grid in a plan for 64 frames (1024 tiles of 32 x 32 per
+    full launch) is tiled 32 columns wide; two frames through that plan
+    (ragged rows: nz = 120) match the oracle, and a one-frame plan of the
+    same grid keeps 16-column tiles with the same results."""
+    wl = synth.workload("cfg1", nz=120, z1_m=18.75e-3)
+    rf = _frames(wl, [21, 22])
+    ref = None
+    for mb, tile in ((64, 32), (1, 16)):
+        out, info, deq = run_gpu(wl, rf, k, rf_dtype=dtype, compensated=int(dtype != "f32"),
+                                 max_batch=mb)
+        assert info["tile_x"] == tile, (mb, info["tile_x"])
+        assert info["device_error_flags"] == 0
+        # against the oracle on the dequantised RF: the FP32 bar for both forms
+        assert_parity(compare(out, oracle_frames(wl, deq, k)), TOL32, what=f"k={k} max_batch={mb}")
+        if ref is None:
+            ref = out
+        else:
+            assert np.max(np.abs(out[:, 0] - ref[:, 0])) <= 1e-5 * np.max(np.abs(ref[:, 0]))
+
+
 def test_pixels_beyond_the_record_and_t0():
     """Short records (many delays fall off the end) and t0 > 0 (negative
     delays near the array): those channels must drop out exactly."""
