@@ -223,38 +223,59 @@ static_assert(kC == 4, "channel-base loads below read 2 x int4");
 // address of sample 0 of the channel's window, so the slot of sample n0 lives
 // at s_cb[cv] + 8 n0 (lattice table); with the full table, whose entries
 // hold n0 - lo, it is the address of the window's first slot.  Work is
-// spread over the whole block, four slots per thread-iteration.
+// spread over the whole block, four slots per thread-iteration.  A first
+// pass writes, per staged channel, the frame-relative index of its window's
+// first sample when the whole window (and the sample after it) lies inside
+// the record and vector loads apply, else -1 (s_off); after one barrier the
+// iterations of those channels need no bounds checks or row arithmetic.
 template <int DT>
 __device__ __forceinline__ void stage_chunk(const BfParams& p, int frame, int tile_id, int v0,
-                                            int* s_cb, unsigned char* smem, uint32_t sbase) {
+                                            int* s_cb, int* s_off, unsigned char* smem,
+                                            uint32_t sbase) {
+  constexpr size_t kElt = DT == PA_RF_F32 ? 4 : 2;
   const int W = p.window, W4 = W >> 2;
   const int ns = p.n_samples;
   const int* lo_t = p.lo + (size_t)tile_id * p.nv;
   const size_t frame_base = (size_t)frame * p.n_elem;
+  const void* frame_rf = reinterpret_cast<const char*>(p.rf) + frame_base * (size_t)ns * kElt;
   for (int c = threadIdx.x; c < p.ncs; c += blockDim.x) {
     const int v = v0 + c;
-    const int lo = v < p.nv && !p.full ? __ldg(lo_t + v) : 0;
-    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - lo * 8;
+    const int lo = v < p.nv ? __ldg(lo_t + v) : 0;
+    s_cb[c] = (int)sbase + p.pairs_off + c * W * 8 - (p.full ? 0 : lo * 8);
+    const int i = v + p.u0;
+    const long long o = (long long)i * ns + lo;
+    const bool inside = p.vec_ok && v < p.nv && i >= 0 && i < p.n_elem && lo >= 0 &&
+                        lo + 4 * W4 <= ns - 1 && o + 4 * W4 < 0x7fffffffll;
+    s_off[c] = inside ? (int)o : -1;
   }
+  __syncthreads();
   const int total = p.ncs * W4;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int cv = (int)(((unsigned)idx * (unsigned)p.w4_inv) >> 20);  // idx / W4
     const int q = idx - cv * W4;
-    const int v = v0 + cv;
-    const int i = v + p.u0;
-    const bool real = v < p.nv && i >= 0 && i < p.n_elem;
-    const int n = (v < p.nv ? __ldg(lo_t + v) : 0) + 4 * q;
+    const int off = s_off[cv];
     float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (real) {
-      const size_t row = (frame_base + i) * (size_t)ns;
-      if (p.vec_ok && n >= 0 && n + 4 <= ns - 1) {
-        rf_load4<DT>(p.rf, row + n, r);
-        r[4] = rf_load<DT>(p.rf, row + n + 4);
-      } else {
+    if (off >= 0) {
+      const size_t e = (size_t)(unsigned)(off + 4 * q);
+      rf_load4<DT>(frame_rf, e, r);
+      r[4] = rf_load<DT>(frame_rf, e + 4);
+    } else {
+      // a window that leaves the record, a virtual channel, or unaligned rows
+      const int v = v0 + cv;
+      const int i = v + p.u0;
+      const bool real = v < p.nv && i >= 0 && i < p.n_elem;
+      const int n = (v < p.nv ? __ldg(lo_t + v) : 0) + 4 * q;
+      if (real) {
+        const size_t row = (size_t)i * (size_t)ns;
+        if (p.vec_ok && n >= 0 && n + 4 <= ns - 1) {
+          rf_load4<DT>(frame_rf, row + n, r);
+          r[4] = rf_load<DT>(frame_rf, row + n + 4);
+        } else {
 #pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          const int k = n + t;
-          if (k >= 0 && k < ns) r[t] = rf_load<DT>(p.rf, row + k);
+          for (int t = 0; t < 5; ++t) {
+            const int k = n + t;
+            if (k >= 0 && k < ns) r[t] = rf_load<DT>(frame_rf, row + k);
+          }
         }
       }
     }
@@ -659,9 +680,9 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
         }
       } else {
         __syncthreads();
-        if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
-        else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
-        else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * p.nc, s_cb, smem, sbase);
+        if (p.rf_dtype == PA_RF_F32) stage_chunk<PA_RF_F32>(p, frame, tile_id, k * p.nc, s_cb, s_lo, smem, sbase);
+        else if (p.rf_dtype == PA_RF_BF16) stage_chunk<PA_RF_BF16>(p, frame, tile_id, k * p.nc, s_cb, s_lo, smem, sbase);
+        else stage_chunk<PA_RF_F16>(p, frame, tile_id, k * p.nc, s_cb, s_lo, smem, sbase);
         __syncthreads();
       }
       const int cu0 = p.u0 + k * p.nc;
