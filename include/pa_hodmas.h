@@ -540,7 +540,7 @@ const char* pa_status_str(pa_status status);
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* pa_last_error(void);
 /* ABI version (major * 100 + minor). */
-int32_t pa_version(void);  /* 104: full per-pixel delay table */
+int32_t pa_version(void);  /* 105: kernel timing inside CUDA graphs, fused-kernel-only mode */
 
 #ifdef __cplusplus
 }

@@ -2063,6 +2063,6 @@ const char* pa_status_str(pa_status s) {
 
 const char* pa_last_error(void) { return g_err.c_str(); }
 
-int32_t pa_version(void) { return 104; }
+int32_t pa_version(void) { return 105; }
 
 }  // extern "C"

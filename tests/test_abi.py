@@ -40,7 +40,7 @@ def test_library_exports_every_declared_function():
 
 def test_version_and_status_strings():
     L = _native.load()
-    assert L.pa_version() >= 100
+    assert L.pa_version() >= 105
     assert L.pa_status_str(0) == b"ok"
     assert L.pa_status_str(1) == b"invalid argument"
 
