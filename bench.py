@@ -9,6 +9,9 @@ compression; FP32 RF.  A step beamforms ``--frames`` seeded synthetic frames
 Metric: Gpixel.ch/s = nx * nz * N * frames / time.  ``value`` is device
 time (CUDA events around each step on the launching stream, inputs resident
 in HBM, L2 flushed by a 256 MiB write between steps, outside the events).
+The steps run through the default CUDA-graph launch; the roofline's fused
+kernel time comes from event-record nodes around that kernel inside the
+same graphs.
 ``e2e`` is the same metric through ``pa_beamform_host`` (pinned host RF in,
 log images out, copies inside the timed region).
 
