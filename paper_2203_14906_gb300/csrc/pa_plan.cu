@@ -611,7 +611,9 @@ void configure(pa_plan_s* P) {
   // launch, 32 -> 8 rows): cfg2 FP32 k = 1, 2 0.594 -> 0.488 ms, k = 3
   // 0.651 -> 0.641 ms, k = 4 0.701 -> 0.692 ms, k = 5 0.831 -> 0.837 ms,
   // k = 7 1.280 -> 1.339 ms; cfg5 (apodised) 2.91 -> 3.06 ms; 16-row groups
-  // were never the fastest.  PA_LANE_ROWS=32|16|8 picks one, for comparisons.
+  // were never the fastest, and 4-row groups (8 slots per warp) were slower
+  // still (k = 2 0.488 -> 0.615 ms, k = 3 0.619 -> 0.671 ms).
+  // PA_LANE_ROWS=32|16|8 picks one, for comparisons.
   P->lane_rows_log2 = (B % 4 == 0 && !P->apod && P->K <= 4) ? 3 : 5;
   // Compensated sums keep their Kahan totals in TMEM; its accesses are
   // warp-wide, so every lane of a warp must run the same channel steps:
