@@ -381,6 +381,19 @@ def test_kernel_timing_in_both_launch_modes():
         again = pa.beamform(plan, rf, 7)
         assert plan.profile_read()["bf_fused"][1] == 0
         assert torch.equal(again, ref)
+        # the host-buffer path, timed (pinned buffers: per-chunk graphs
+        # instead of the whole-call graph) and untimed
+        rf_h = rf.cpu().pin_memory()
+        out_h = torch.empty(tuple(ref.shape), dtype=torch.float32).pin_memory()
+        plan.profile(True, fused_only=True)
+        pa.beamform_host(plan, rf_h, 7, out=out_h)
+        prof = plan.profile_read()
+        plan.profile(False)
+        assert prof["bf_fused"][1] >= 1 and prof["post"][1] == 0, prof
+        assert torch.equal(out_h, ref.cpu())
+        out_h.zero_()
+        pa.beamform_host(plan, rf_h, 7, out=out_h)
+        assert torch.equal(out_h, ref.cpu())
         from paper_2203_14906_gb300._native import check
 
         with pytest.raises(pa.PAError):
