@@ -898,8 +898,70 @@ def serving_legs(pa, args, local):
     noise = max(b["gpixel_ch_per_s"]["spread_of_median"], f["gpixel_ch_per_s"]["spread_of_median"])
     out["saturation_bf16_kahan_vs_fp32"] = {
         "ratio": ratio, "run_to_run_spread": noise,
-        "difference_exceeds_spread": abs(ratio - 1.0) > noise}
+        "difference_exceeds_spread": abs(ratio - 1.0) > noise,
+        "note": "the forms' legs ran one after the other; see paired_forms"}
+    out["paired_forms"] = paired_forms(pa, args, local)
     return out
+
+
+def paired_forms(pa, args, local, pairs=5, n_sat=4000, offered_pairs=4):
+    """The two forms measured in pairs on one server that holds both forms'
+    plans (warm): runs alternate BF16 + Kahan / FP32 in ABBA order, each on
+    its own request set, so that a drift of the box over the process weighs
+    on both forms alike.  Saturation (every request queued at once): each
+    pair's throughput ratio.  The stated trace (--serve-rate Poisson): each
+    pair's p50 / p99.  A difference holds when every pair lies on the same
+    side."""
+    from paper_2203_14906_gb300.serving import Server
+
+    sets = {"bf16_kahan": _ServeSet(pa, "bf16", 1), "fp32": _ServeSet(pa, "f32", 0)}
+    sat_reqs = {k: [ss.requests(n_sat, 331 + r, 1e6) for r in range(pairs)]
+                for k, ss in sets.items()}
+    off_reqs = {k: [ss.requests(args.serve_requests, 431 + r, args.serve_rate)
+                    for r in range(offered_pairs)] for k, ss in sets.items()}
+    sat = {k: [] for k in sets}
+    off = {k: [] for k in sets}
+
+    def order(r):
+        return ("bf16_kahan", "fp32") if r % 2 == 0 else ("fp32", "bf16_kahan")
+
+    with Server(**SERVER_CFG, stages=pa.PA_STAGE_LOG) as srv:
+        for ss in sets.values():
+            ss.warm(srv)
+        for r in range(pairs):
+            for k in order(r):
+                sat[k].append(sets[k].replay(srv, sat_reqs[k][r], False, local))
+        for r in range(offered_pairs):
+            for k in order(r):
+                off[k].append(sets[k].replay(srv, off_reqs[k][r], True, local))
+    ratios = [a["gpixel_ch_per_s"] / b["gpixel_ch_per_s"]
+              for a, b in zip(sat["bf16_kahan"], sat["fp32"])]
+    p99 = {k: [r["latency_ms_p99"] for r in off[k]] for k in off}
+    p99_ratio = [a / b for a, b in zip(p99["bf16_kahan"], p99["fp32"])]
+
+    def same_side(v):
+        return all(x > 1.0 for x in v) or all(x < 1.0 for x in v)
+
+    return {
+        "server": "one server, both forms' plans resident", "order": "ABBA...",
+        "saturation": {
+            "pairs": pairs, "frames_per_run": n_sat,
+            "bf16_kahan_gpixel_ch_per_s": [r["gpixel_ch_per_s"] for r in sat["bf16_kahan"]],
+            "fp32_gpixel_ch_per_s": [r["gpixel_ch_per_s"] for r in sat["fp32"]],
+            "bf16_kahan_frames_per_s": [r["served_frames_per_s"] for r in sat["bf16_kahan"]],
+            "fp32_frames_per_s": [r["served_frames_per_s"] for r in sat["fp32"]],
+            "ratio_per_pair": ratios, "ratio_median": float(np.median(ratios)),
+            "every_pair_same_side": same_side(ratios)},
+        "offered": {
+            "pairs": offered_pairs, "frames_per_run": args.serve_requests,
+            "offered_frames_per_s": args.serve_rate,
+            "bf16_kahan_p50_ms": [r["latency_ms_p50"] for r in off["bf16_kahan"]],
+            "fp32_p50_ms": [r["latency_ms_p50"] for r in off["fp32"]],
+            "bf16_kahan_p99_ms": p99["bf16_kahan"], "fp32_p99_ms": p99["fp32"],
+            "p99_ratio_per_pair": p99_ratio, "p99_ratio_median": float(np.median(p99_ratio)),
+            "every_pair_same_side": same_side(p99_ratio)},
+        "plans_resident": sorted({r["plans_resident"] for d in (sat, off) for k in d for r in d[k]}),
+        "sm_mhz_median": sorted({r["sm_mhz_median"] for d in (sat, off) for k in d for r in d[k]})}
 
 
 def run_ours(args):
