@@ -617,8 +617,22 @@ __global__ void __launch_bounds__(256, (MinBlocks<K, COMP>::value))
     // with channel u + c) are two 16-byte pairs, pixels 0-1 at fbase0 +
     // (u - u0) fstep and pixels 2-3 half a step further (fhalf): per tile,
     // step and half, the threads' pairs are contiguous.
-    const int2* tcol = p.table + z;
-    const float* wcol = APOD ? p.wtab + z : nullptr;
+    // The depth-blocked table layout is only ever chosen for orders <= 2 and
+    // compensated plans without apodisation; the other instantiations keep
+    // the row-major address (their code measured faster without the general
+    // form).
+    constexpr bool TBLOCKED = (K <= 2 || COMP) && !APOD;
+    const int2* tcol;
+    const float* wcol;
+    if constexpr (TBLOCKED) {
+      const size_t trow0 =  // table row 0 at depth z
+          (size_t)(z >> p.table_zshift) * (size_t)p.table_zblock + (z & p.table_zmask);
+      tcol = p.table + trow0;
+      wcol = nullptr;
+    } else {
+      tcol = p.table + z;
+      wcol = APOD ? p.wtab + z : nullptr;
+    }
     const int row_u0 = jt - p.dmin;
     const int mstride = p.m * p.table_stride;
     const size_t fhalf = (size_t)32 * p.slots * 2;

@@ -56,10 +56,15 @@ __host__ __device__ constexpr int tmem_columns(int warps, int na) {
 // TMEM columns of one SM.
 constexpr int kTmemColsPerSm = 512;
 
-// Delay-table layout: row t = d - dmin (lattice offset d), depth z fastest,
-// so a warp's 32 depth rows read one contiguous 256-byte run per step.
-__host__ __device__ __forceinline__ size_t table_index(int t, int z, int nzp) {
-  return (size_t)t * nzp + z;
+// Delay-table layout, row t = d - dmin (lattice offset d), depth z:
+// zb = 0: row-major, depth fastest (nzp entries per row);
+// zb > 0: depth blocks of 2^zb rows, within a block row-major.  With 8-row
+// lane groups and zb = 3 a warp's step loads (8 depth rows of 4 neighbouring
+// lattice rows) are one contiguous 256-byte run instead of four 64-byte
+// pieces.
+__host__ __device__ __forceinline__ size_t table_index(int t, int z, int ndrows, int nzp, int zb) {
+  if (zb == 0) return (size_t)t * nzp + z;
+  return (((size_t)(z >> zb) * ndrows + t) << zb) + (z & ((1 << zb) - 1));
 }
 
 // Parameters of the fused gather + interpolate + root + power-sum kernel.
@@ -88,7 +93,7 @@ struct BfParams {  // aligned as CUtensorMap requires
   int full;               // 1: full table (channel bases are window starts)
   int steps;              // channel steps u1 - u0
   const float* wtab;      // [ndrows][nz_pad] apodisation weight (or null)
-  int table_stride;       // nz_pad
+  int table_stride;       // entries between lattice rows at one depth (nz_pad or 2^zb)
   const int4* items;      // [n_tiles * ngroups] {tile_id, grp, tx, tz}, deepest first
   const int2* slot_rg;    // [slots] {column residue r_m, column group g}
   int ndrows;
@@ -118,6 +123,11 @@ struct BfParams {  // aligned as CUtensorMap requires
   int* timeouts;          // running count of blocks whose bounded TMA wait ran out
   int expect_extra;       // bytes added to every chunk's expected transaction
                           // count: 0, or > 0 only to test the bounded wait
+  // entry of table row 0 at depth z: (z >> table_zshift) * table_zblock +
+  // (z & table_zmask) (row-major: shift 31, block 0, all-ones mask)
+  int table_zshift, table_zmask;
+  long long table_zblock;
+  int table_zb, table_nzp;  // the layout for table_index (zb 0: row-major)
 };
 
 // Post-filter / envelope parameters (one warp per depth column).

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_lanes(const __grid_constant__ BfParams 
     for (int q = 0; q < NA; ++q) acc[q] = 0.f;
     for (int i = g; i < p.n_elem; i += L) {
       const int d = j - p.m * i;
-      const int2 e = __ldg(p.table + (size_t)(d - p.dmin) * p.table_stride + z);
+      const int2 e = __ldg(p.table + table_index(d - p.dmin, z, p.ndrows, p.table_nzp, p.table_zb));
       const int addr = s_cb[i - p.u0] + e.x;
       float2 r;
       asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));

@@ -158,6 +158,7 @@ struct pa_plan_s {
   std::vector<GraphEntry> graphs;
   bool use_graph = true;
   int lane_rows_log2 = 5;  // depth rows per lane group of the fused kernel (log2)
+  int table_zb = 0;        // lattice table layout: 0 row-major, else log2 depth-block height
   // kernel timing (pa_plan_profile): bit k set = kernel kind k is timed
   uint32_t prof = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
@@ -225,7 +226,7 @@ __host__ __device__ __forceinline__ int full_column(const FullGeom& f, int tx, i
 }
 
 struct TableGeom {
-  int ndrows, nzp, dmin, ns, nearest;
+  int ndrows, nzp, dmin, ns, nearest, zb;
   double x_const;  // x0 + (N-1)/2 pitch: dx of lattice offset d is x_const + (d + 1/2) dx
   double dx, z0, dz, fs, c, t0, fnum;
   // full table: element i = v + u0 of N at x_i = (i - (N-1)/2) pitch
@@ -291,7 +292,7 @@ __global__ void k_table(TableGeom g, int2* table, float* wtab) {
   int n0;
   double a;
   delay_sample(g, dxv, zp, &n0, &a);
-  const size_t ti = table_index(row, z, g.nzp);
+  const size_t ti = table_index(row, z, g.ndrows, g.nzp, g.zb);
   table[ti] = make_int2(n0 * 8, __float_as_int((float)a));
   if (wtab) wtab[ti] = apod_weight(g, dxv, zp);
 }
@@ -349,7 +350,7 @@ __global__ void k_count_active_full(FullGeom f, const float* wtab, unsigned long
 }
 
 struct TileGeom {
-  int nxt, nzt, tile_x, tile_z, m, dmin, nzp, nv, u0, ndrows;
+  int nxt, nzt, tile_x, tile_z, m, dmin, nzp, nv, u0, ndrows, zb;
   int full;  // 1: full table (laid out as full_index says)
 };
 
@@ -376,8 +377,8 @@ __global__ void k_windows(TileGeom g, int lo_align, const int2* table, int* lo, 
       atomicOr(err, 4);
       continue;
     }
-    mn = min(mn, table[table_index(row, zf, g.nzp)].x >> 3);
-    mx = max(mx, table[table_index(row, zl, g.nzp)].x >> 3);
+    mn = min(mn, table[table_index(row, zf, g.ndrows, g.nzp, g.zb)].x >> 3);
+    mx = max(mx, table[table_index(row, zl, g.ndrows, g.nzp, g.zb)].x >> 3);
   }
   const int lo_al = mn & ~(lo_align - 1);  // lo_align is a power of two
   lo[(size_t)tile * g.nv + v] = lo_al;
@@ -431,7 +432,7 @@ __global__ void k_uranges(TileGeom g, FullGeom f, int slots, int u1, int kc, con
           on |= wtab[full_index(f, tile, u - g.u0, c, sl, g.tile_z - 1)] > 0.f;
       } else {
         const int row = tile_row(g, jt, u - g.u0);
-        if (row >= 0 && row < g.ndrows) on = wtab[table_index(row, zl, g.nzp)] > 0.f;
+        if (row >= 0 && row < g.ndrows) on = wtab[table_index(row, zl, g.ndrows, g.nzp, g.zb)] > 0.f;
       }
       if (on) {
         ua = min(ua, u);
@@ -463,7 +464,7 @@ __global__ void k_count_active(TileGeom g, int nx, int nz, int n, const float* w
   if (z < nz) {
     for (int i = 0; i < n; ++i) {
       const int row = tile_row(g, j, i - g.u0);
-      if (wtab[table_index(row, z, g.nzp)] > 0.f) ++c;
+      if (wtab[table_index(row, z, g.ndrows, g.nzp, g.zb)] > 0.f) ++c;
     }
   }
   for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(0xffffffffu, c, s);
@@ -623,6 +624,19 @@ void configure(pa_plan_s* P) {
     const int want = atoi(e) == 8 ? 3 : (atoi(e) == 16 ? 4 : 5);
     if (B % (1 << (5 - want)) == 0 && !(P->tmem_cols && P->apod)) P->lane_rows_log2 = want;
   }
+  // Lattice table layout: depth blocks of 8 rows (a warp's four lattice
+  // rows at one step in one contiguous 256-byte run: half the L1 wavefronts
+  // of four 64-byte pieces) where that measured faster, row-major elsewhere.
+  // Measured on GB300 (fused kernel per launch, one run, against row-major):
+  // cfg2 k = 1, 2 0.488 -> 0.458 ms (bound by the L1 data pipe), BF16 +
+  // Kahan k = 3 0.662 -> 0.653 ms, cfg3 BF16 + Kahan 1.261 -> 1.236 ms; but
+  // plain FP32 k = 3 0.617 -> 0.628 ms, and blocks of 32 rows were slower
+  // than row-major for every plan tried (k = 5 0.819 -> 0.838 ms, the cfg5
+  // batch 2.675 -> 2.790 ms) although a warp's loads have the same shape.
+  // (8-row lane groups imply no apodisation; the fused kernel computes the
+  // blocked address only in the instantiations for k <= 2 or compensated
+  // sums without apodisation.)
+  P->table_zb = (P->lane_rows_log2 == 3 && !P->apod && (P->K <= 2 || P->comp)) ? 3 : 0;
   P->threads = 32 * B;
   P->tile_x = P->m * kC * P->R;
   P->tile_z = 32;
@@ -855,6 +869,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   TableGeom tg;
   tg.ndrows = P->ndrows;
   tg.nzp = P->nz_pad;
+  tg.zb = P->table_zb;
   tg.dmin = P->dmin;
   tg.ns = d.n_samples;
   tg.nearest = d.interp == PA_INTERP_NEAREST;
@@ -884,6 +899,7 @@ pa_status build_plan(pa_plan_s* P, cudaStream_t st) {
   g.nv = P->nv;
   g.u0 = P->u0;
   g.ndrows = P->ndrows;
+  g.zb = P->table_zb;
   g.full = P->full ? 1 : 0;
   FullGeom fg{P->nxt, P->n_tiles, P->tile_x, P->tile_z, P->m, P->slots, P->u1 - P->u0,
               P->lane_rows_log2, d.nx, d.nz, d.n_elem, P->u0, P->nv};
@@ -1197,7 +1213,12 @@ pa_status prepare_chunk(pa_plan_s* P, const void* rf, int nf, float* out, uint32
   b.full = P->full ? 1 : 0;
   b.steps = P->u1 - P->u0;
   b.wtab = P->wtab;
-  b.table_stride = P->nz_pad;
+  b.table_stride = P->table_zb ? 1 << P->table_zb : P->nz_pad;
+  b.table_zb = P->table_zb;
+  b.table_nzp = P->nz_pad;
+  b.table_zshift = P->table_zb ? P->table_zb : 31;
+  b.table_zmask = P->table_zb ? (1 << P->table_zb) - 1 : 0x7fffffff;
+  b.table_zblock = P->table_zb ? (long long)P->ndrows << P->table_zb : 0;
   b.items = P->items;
   b.slot_rg = P->slot_rg;
   b.ndrows = P->ndrows;
