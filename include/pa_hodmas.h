@@ -24,6 +24,8 @@
  *   root      x_i = sgn(s_i) |s_i|^(1/k) (signed even roots as in Eqs. 2, 5;
  *             real odd roots as in Eqs. 4, 6)
  *   combine   e_k of the x_i by Newton's identities from power sums, in FP64
+ *             (for k = 4, 5 the term p2^2 - 2 p4 enters as one FP32 value
+ *             formed with an error-free square, as DMAS is)
  *   post      per depth column: zero-pad to M = 2^ceil(log2 nz), FFT, multiply
  *             by a raised-cosine band (f0 +- f0/2 for DAS and odd orders,
  *             2 f0 +- f0/2 for even orders, roll-off f0/4, clipped at the
