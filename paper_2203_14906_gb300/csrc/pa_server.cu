@@ -228,13 +228,27 @@ struct pa_server_s {
   }
 
   // Try to issue one batch on slot s; returns true if something was issued
-  // or failed (the visible list changed).
+  // or failed (the visible list changed).  The scan walks the queue in
+  // arrival order; a request whose plan was already found unable to run in
+  // this scan (being built, in flight, held back by the TMEM rule, or
+  // waiting for memory for its build) is passed over by comparing its key
+  // with those plans' keys, without another lookup in the plan map: with
+  // many requests queued behind a few busy plans, a lookup per request made
+  // each scheduler pass, and so the reaping of finished batches, slower.
   bool issue(Slot& s) {
     // a TMEM-dense request waiting for the compensated batches in flight to
     // drain holds back later compensated requests, so it is not starved
     bool hold_comp = false;
+    std::vector<const Request*> blocked;  // one request per plan that cannot run now
+    auto is_blocked = [&](const Request* r) {
+      for (const Request* b : blocked)
+        if (b->key_hash == r->key_hash && b->key == r->key) return true;
+      return false;
+    };
     for (auto it = visible.begin(); it != visible.end(); ++it) {
       Request* head = *it;
+      if (is_blocked(head)) continue;
+      blocked.push_back(head);  // taken back out below if the request runs
       auto pit = plans.find(head->key);
       if (pit == plans.end()) {
         // new descriptor: reserve the plan's memory and queue its build;
@@ -271,6 +285,7 @@ struct pa_server_s {
           continue;
         }
       }
+      blocked.pop_back();
       std::vector<std::list<Request*>::iterator> pick{it};
       for (auto jt = std::next(it); jt != visible.end() && (int)pick.size() < cfg.max_batch; ++jt)
         if ((*jt)->key_hash == head->key_hash && (*jt)->key == head->key) pick.push_back(jt);
@@ -457,7 +472,9 @@ struct pa_server_s {
       if (!stop) {
         for (auto& s : slots) {
           if (s.busy || visible.empty()) continue;
-          progress = issue(s) || progress;
+          // what one free slot cannot issue, no other free slot can in this pass
+          if (!issue(s)) break;
+          progress = true;
         }
       }
       if (!progress) {
