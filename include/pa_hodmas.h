@@ -53,7 +53,7 @@ typedef enum {
   PA_ENOMEM = 2,        /* device allocation failed or budget exceeded    */
   PA_ECUDA = 3,         /* CUDA runtime error (pa_last_error has detail)  */
   PA_ETIMEOUT = 4,      /* a bounded wait ran out                         */
-  PA_EUNSUPPORTED = 5,  /* valid request outside what this build handles  */
+  PA_EUNSUPPORTED = 5,  /* valid request outside what the library handles */
   PA_EBUSY = 6          /* resource in use (e.g. server queue full)       */
 } pa_status;
 
