@@ -1,6 +1,8 @@
-"""Host logic of bench.py's precision report (CPU): the per-image error
+"""Host logic of bench.py (CPU): the precision report's per-image error
 measures against the FP64 oracle, checked on oracle images with errors of
-known size planted in them."""
+known size planted in them; and the roofline accounting - the committed
+DRAM-traffic record is used only for the kernel source and launch shape it
+was taken on, and the per-pair operation model."""
 
 import numpy as np
 
@@ -57,3 +59,55 @@ def test_headline_form_switch():
     assert bench.form_dtype(A) == ("f32", 0)
     A.form = "precision"
     assert bench.form_dtype(A) == ("bf16", 1)
+
+
+# ---- roofline accounting: the DRAM-traffic record and the per-pair model
+
+
+def _fake_sources(tmp_path, body):
+    csrc = tmp_path / "csrc"
+    csrc.mkdir(exist_ok=True)
+    (csrc / "pa_bf_kernel.cuh").write_text(body)
+    (csrc / "pa_internal.cuh").write_text("int x;\n")
+    (csrc / "pa_post.cu").write_text("not hashed\n")
+    return str(csrc)
+
+
+def test_kernel_hash_ignores_comments_and_spacing_only(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "CSRC", _fake_sources(tmp_path, "int f() { return 1; } // one\n"))
+    h0 = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "CSRC", _fake_sources(tmp_path, "/* a\nb */ int  f()\n{ return 1; }\n"))
+    assert bench.kernel_source_hash() == h0
+    monkeypatch.setattr(bench, "CSRC", _fake_sources(tmp_path, "int f() { return 2; }\n"))
+    assert bench.kernel_source_hash() != h0
+    (tmp_path / "csrc" / "pa_post.cu").write_text("changed, still not hashed\n")
+    h1 = bench.kernel_source_hash()
+    (tmp_path / "csrc" / "pa_post.cu").write_text("changed again\n")
+    assert bench.kernel_source_hash() == h1
+
+
+def test_traffic_record_is_used_only_for_the_kernel_and_launch_it_was_taken_on(tmp_path,
+                                                                             monkeypatch):
+    import json
+
+    monkeypatch.setattr(bench, "CSRC", _fake_sources(tmp_path, "int f() { return 1; }\n"))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    launch = {f: i + 1 for i, f in enumerate(bench.LAUNCH_FIELDS)}
+    assert bench.measured_traffic("dram_bytes_per_launch", launch) is None  # no record
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel_hash": bench.kernel_source_hash(), "launch": dict(launch),
+           "dram_bytes_per_launch": 1234}
+    (tmp_path / "profiles" / "bf_fused_traffic.json").write_text(json.dumps(rec))
+    assert bench.measured_traffic("dram_bytes_per_launch", launch) == 1234
+    other = dict(launch, chunk_steps=launch["chunk_steps"] + 1)
+    assert bench.measured_traffic("dram_bytes_per_launch", other) is None
+    rec["kernel_hash"] = "0" * 16
+    (tmp_path / "profiles" / "bf_fused_traffic.json").write_text(json.dumps(rec))
+    assert bench.measured_traffic("dram_bytes_per_launch", launch) is None
+
+
+def test_operations_per_pair_model():
+    """2k + 7 for the combined DAS + DMAS + DMAS-k pass (13 at k = 3, 17 at
+    k = 5, as Table 1's per-channel counts add up); k <= 2 reuse the DMAS
+    sums."""
+    assert [bench.ops_per_pair(k) for k in (1, 2, 3, 4, 5, 8)] == [7, 9, 13, 15, 17, 23]
